@@ -1,0 +1,198 @@
+/*
+ * srdr.h — C ABI of the GB300 (sm_103a) library for the splitting
+ * random-choice dynamic relaxation of Total-Lagrangian SPH
+ * (Zhu, Zhang & Hu, "A splitting random-choice dynamic relaxation method for
+ * smoothed particle hydrodynamics", arXiv 2103.08932).
+ *
+ * Problem statement (Sec. 2.1, Sec. 4 intro): an elastic body given by
+ * particles on its reference configuration, smoothing length h = 1.3 dp,
+ * fixed reference neighbours 0 < |r0_ij| < 2h, loaded by a body force, is
+ * relaxed to static equilibrium by the TL-SPH step (Sec. 2.2-2.3) plus the
+ * operator-split implicit artificial-viscosity damping (Sec. 3.1) applied on
+ * randomly chosen steps (Sec. 3.3) and swept colour by colour over the
+ * splitting cell-linked list (Sec. 3.4).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an srdr_status; no C++ exception crosses the ABI.
+ *    On failure srdr_last_error() returns a message (thread-local, valid
+ *    until the next call on the same thread).
+ *  - Host arrays passed in are caller-owned and only read during the call.
+ *    Host arrays passed out are caller-owned and must hold the stated number
+ *    of elements; the library never keeps a pointer to them.
+ *  - Particle arrays are in ORIGINAL particle order, FP64, row-major [n][3]
+ *    for vectors (the third component is ignored / written as 0 in 2D).
+ *  - The library owns all device memory of a body (and of a server) and frees
+ *    it in the matching destroy call.
+ *  - A handle is not thread-safe; the server is internally synchronised.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream); all
+ *    device work of a handle is ordered on it.
+ */
+#ifndef SRDR_H
+#define SRDR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SRDR_OK = 0,
+    SRDR_ERR_INVALID = -1,       /* bad argument or body (e.g. singular correction matrix) */
+    SRDR_ERR_NO_MEMORY = -2,     /* device allocation or memory admission refused */
+    SRDR_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    SRDR_ERR_NOT_CONVERGED = -4, /* step cap reached before the KE criterion */
+    SRDR_ERR_NONFINITE = -5,     /* kinetic energy became NaN or Inf */
+    SRDR_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    SRDR_ERR_BUSY = -7           /* server queue full / result not ready */
+} srdr_status;
+
+enum { SRDR_LINEAR_SVK = 0, SRDR_NEO_HOOKEAN = 1 };
+enum { SRDR_FP64 = 0, SRDR_FP32_MIXED = 1 };
+enum { SRDR_DAMP_NONE = 0, SRDR_DAMP_PARTICLE = 1, SRDR_DAMP_PAIRWISE = 2 };
+enum { SRDR_FLAG_CONSTRAINED = 1, SRDR_FLAG_END_LOAD = 2 };
+
+/*
+ * Body description (POD, caller-owned, copied by the create calls).
+ *
+ * Lattice bodies (srdr_body_create): particles at (i + 1/2) dp filling
+ * [0, extent[a]) on each axis; clamp_layers extra layers below 0 on
+ * clamp_axis are constrained (v = 0, u = 0); presc_layers extra layers beyond
+ * extent on clamp_axis are held at displacement presc_disp and the body
+ * starts from the linear interpolation between the two faces;
+ * end_load_layer != 0 adds end_load to the last body layer on clamp_axis.
+ * Particle order: z outermost, y, x innermost, constrained layers included.
+ *
+ * material, rho0, E, nu: Sec. 2.1 (Eqs. constitutive-equation, strain-density;
+ *   E = 2 mu (1 + nu), 2D is plane strain).
+ * h_over_dp: smoothing length h = h_over_dp * dp (1.3 in Sec. 4).
+ * beta, L_char: eta = beta/4 sqrt(rho0 E) L_char (Eq. viscous-parameter).
+ * alpha, seed: random choice (Eq. viscosity-reset): step n is damped with
+ *   eta~ = eta / alpha iff phi_n < alpha, phi_n from Philox4x64-10 with
+ *   counter (n, 0, 0, 0) and key (seed, 0), top 53 bits of word 0 / 2^53.
+ * damping: SRDR_DAMP_PARTICLE is the particle-by-particle scheme (Sec. 3.1),
+ *   SRDR_DAMP_PAIRWISE the pairwise scheme (Sec. 3.2).
+ * precision: SRDR_FP64 computes everything in FP64; SRDR_FP32_MIXED runs the
+ *   neighbour sums, stress and damping in FP32 and keeps the displacement as
+ *   an FP32 hi/lo pair (about 48 significant bits) and the kinetic-energy
+ *   reduction in FP64.
+ * dt: > 0 fixes the time step; 0 uses Eq. time-step-criterion with
+ *   |v|max = 0 and |a|max = the largest body force, min'd with the implicit
+ *   viscous limit 50 h^2 / (nu~ D) of Eq. viscous-criteria, nu~ = eta/(alpha rho0).
+ */
+typedef struct {
+    int dim;
+    double extent[3];
+    double dp;
+    int clamp_axis;     /* -1: none */
+    int clamp_layers;
+    int presc_layers;
+    double presc_disp[3];
+    int end_load_layer;
+    int material;
+    double rho0, E, nu;
+    double h_over_dp;
+    double gravity[3];
+    double end_load[3];
+    double beta, L_char, alpha;
+    uint64_t seed;
+    int damping;
+    int precision;
+    double dt;
+} srdr_body_desc;
+
+typedef struct srdr_body srdr_body;
+
+/* Build a lattice body from desc: particles (Sec. 4), splitting cell-linked
+ * list and colour split (Sec. 3.4), neighbour CSR and kernel-gradient weights
+ * (Eqs. correction-matrix1), correction matrices B0 (Eq. correction-matrix).
+ * SRDR_ERR_INVALID on a bad desc or a singular correction matrix. */
+srdr_status srdr_body_create(const srdr_body_desc* desc, void* cuda_stream, srdr_body** out);
+
+/* The same from explicit particles: r0[n][3] reference positions, vol[n]
+ * volumes (NULL: dp^dim), flags[n] SRDR_FLAG_* bits (NULL: all free), u0[n][3]
+ * initial displacements (NULL: zero; constrained particles keep theirs).
+ * The lattice fields of desc (extent, clamp_*, presc_*, end_load_layer) are
+ * ignored; dp still sets h and the default volume. */
+srdr_status srdr_body_create_particles(const srdr_body_desc* desc, int64_t n, const double* r0,
+                                       const double* vol, const uint8_t* flags, const double* u0,
+                                       void* cuda_stream, srdr_body** out);
+
+/* Advance nsteps time steps (Sec. 2.3 position-Verlet with the Lie-Trotter
+ * split v(t+dt) = S_d o S_m v(t), Eq. operator-splitting).  Asynchronous on
+ * the body's stream; errors of the device work surface at the next
+ * synchronising call. */
+srdr_status srdr_body_step(srdr_body* body, int64_t nsteps);
+
+/* Step until KE < ke_ratio * KE_max (KE over free particles, FP64, tested
+ * after every step) or max_steps more steps; the state stops at the step that
+ * met the criterion.  SRDR_ERR_NOT_CONVERGED at the cap, SRDR_ERR_NONFINITE if
+ * KE became non-finite.  steps_taken / final_ke_ratio may be NULL. */
+srdr_status srdr_body_relax(srdr_body* body, double ke_ratio, int64_t max_steps,
+                            int64_t* steps_taken, double* final_ke_ratio);
+
+/* Displacement u^n (resp. velocity v^n) at the current full step into
+ * host_out[n][3], original order; n_doubles must be >= 3 n. Synchronises. */
+srdr_status srdr_body_read_displacement(const srdr_body* body, double* host_out, size_t n_doubles);
+srdr_status srdr_body_read_velocity(const srdr_body* body, double* host_out, size_t n_doubles);
+
+/* Overwrite the state at the current full step (checkpoint restore / test
+ * set-up): u[n][3] and v[n][3] in original order, either may be NULL. */
+srdr_status srdr_body_write_state(srdr_body* body, const double* u, const double* v,
+                                  int64_t step_index, double ke_max);
+
+/* Sizes: particles, neighbour pairs, non-empty cells, time step; any may be NULL. */
+srdr_status srdr_body_info(const srdr_body* body, int64_t* n_particles, int64_t* nnz,
+                           int* n_cells, double* dt);
+
+typedef struct {
+    int64_t step;          /* steps taken since creation */
+    int64_t damped_steps;  /* steps on which S_d ran */
+    double ke, ke_max;     /* last step's KE and the running maximum */
+    double eta, dt;        /* artificial viscosity and time step */
+    int converged;         /* last relax met its criterion */
+    int64_t launches;      /* kernels launched by step / relax calls since creation */
+} srdr_stats;
+srdr_status srdr_body_stats(const srdr_body* body, srdr_stats* out);
+
+/* Inspection of the build for tests: neighbour CSR (row_ptr[n+1], col[nnz],
+ * original ids, rows ascending), cell id and colour per particle, and the
+ * canonical sweep order (original ids sorted by colour, cell, id). */
+srdr_status srdr_body_read_neighbours(const srdr_body* body, int64_t* row_ptr, int64_t* col);
+srdr_status srdr_body_read_cells(const srdr_body* body, int64_t* cell, int* colour,
+                                 int64_t* order);
+
+enum { SRDR_FIELD_PB = 0, SRDR_FIELD_B0 = 1 };
+/* Per-particle 3x3 fields, row-major [n][3][3], original order: P B0 from the
+ * last stress pass, or the correction matrix B0. */
+srdr_status srdr_body_read_field(const srdr_body* body, int field, double* host_out,
+                                 size_t n_doubles);
+
+/* Kernel timing with CUDA events recorded on the body's stream around each
+ * kernel class of every step (the damping sweep class spans all colour
+ * launches of one damped step).  srdr_body_profile(body, 1) clears and starts
+ * recording, (body, 0) stops; srdr_body_kernel_times synchronises and returns
+ * the accumulated device milliseconds and launch counts per class. */
+enum { SRDR_K_PASS_A = 0, SRDR_K_PASS_B = 1, SRDR_K_SWEEP = 2, SRDR_K_FINISH = 3, SRDR_K_KE = 4,
+       SRDR_K_NCLASS = 5 };
+typedef struct {
+    double ms[SRDR_K_NCLASS];
+    int64_t launches[SRDR_K_NCLASS];
+    int64_t intervals[SRDR_K_NCLASS];
+} srdr_kernel_times;
+srdr_status srdr_body_profile(srdr_body* body, int enable);
+srdr_status srdr_body_kernel_times(const srdr_body* body, srdr_kernel_times* out);
+
+void srdr_body_destroy(srdr_body* body);
+const char* srdr_last_error(void);
+
+/* The library's own Philox4x64-10 (host side of the device routine):
+ * out[4] = Philox4x64-10(counter, key) and phi_n of the random choice. */
+void srdr_philox4x64_10(const uint64_t counter[4], const uint64_t key[2], uint64_t out[4]);
+double srdr_random_phi(uint64_t seed, uint64_t step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

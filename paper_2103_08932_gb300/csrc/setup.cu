@@ -1,0 +1,703 @@
+// setup.cu — body construction on the GPU: splitting cell-linked list and
+// colour split (Sec. 3.4), fixed reference neighbours with kernel-gradient
+// weights (Eq. correction-matrix1), correction matrices (Eq. correction-matrix)
+// and the sliced-ELL layout streamed by the stress and force passes.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "srdr_internal.cuh"
+
+namespace srdr {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int nblocks(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+// Wendland C2 (h = support / 2): W(q) = a_d (1 - q/2)^4 (1 + 2q), q = r/h < 2, with
+// a_2 = 7 / (4 pi h^2), a_3 = 21 / (16 pi h^3).  Its radial derivative divided
+// by r is W'(r)/r = -5 a_d / h^2 (1 - q/2)^3, free of a division by r.
+__device__ inline double wendland_dw_over_r(int dim, double h, double r)
+{
+    const double pi = 3.14159265358979323846;
+    double a = dim == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
+    double t = 1.0 - 0.5 * (r / h);
+    if (t <= 0.0) return 0.0;
+    return -5.0 * a / (h * h) * t * t * t;
+}
+
+// squared distance, IEEE ops in x, y, z order (no contraction), so that the
+// integer decision 0 < d2 < rc2 is reproducible bit for bit
+__device__ inline double dist2(int dim, const double* r0, int n, int i, int j)
+{
+    double s = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        double d = __dsub_rn(r0[(size_t)a * n + i], r0[(size_t)a * n + j]);
+        s = __dadd_rn(s, __dmul_rn(d, d));
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ bbox
+__global__ void k_bbox_partial(const double* __restrict__ r0aos, int n, double* __restrict__ part)
+{
+    __shared__ double smin[3][kThreads], smax[3][kThreads];
+    int t = threadIdx.x;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * blockDim.x + t; i < n; i += gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            double x = r0aos[(size_t)i * 3 + a];
+            mn[a] = fmin(mn[a], x);
+            mx[a] = fmax(mx[a], x);
+        }
+    for (int a = 0; a < 3; ++a) {
+        smin[a][t] = mn[a];
+        smax[a][t] = mx[a];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][t] = fmin(smin[a][t], smin[a][t + s]);
+                smax[a][t] = fmax(smax[a][t], smax[a][t + s]);
+            }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int a = 0; a < 3; ++a) {
+            part[blockIdx.x * 6 + a] = smin[a][0];
+            part[blockIdx.x * 6 + 3 + a] = smax[a][0];
+        }
+}
+
+__global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], part[b * 6 + a]);
+            mx[a] = fmax(mx[a], part[b * 6 + 3 + a]);
+        }
+    for (int a = 0; a < 3; ++a) {
+        out[a] = mn[a];
+        out[3 + a] = mx[a];
+    }
+}
+
+// ------------------------------------------------------------------ cells
+struct Grid {
+    int dim;
+    int nx, ny, nz;
+    double lo0, lo1, lo2;
+    double rc;
+};
+
+__device__ inline int cell_coord(double x, double lo, double rc, int ncell)
+{
+    double q = floor(__ddiv_rn(__dsub_rn(x, lo), rc));
+    int c = (int)q;
+    if (q < 0.0) c = 0;
+    if (c > ncell - 1) c = ncell - 1;
+    return c;
+}
+
+__global__ void k_cell_hash(const double* __restrict__ r0aos, int n, Grid g, int* __restrict__ cell,
+                            int* __restrict__ count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cx = cell_coord(r0aos[(size_t)i * 3 + 0], g.lo0, g.rc, g.nx);
+    int cy = g.dim >= 2 ? cell_coord(r0aos[(size_t)i * 3 + 1], g.lo1, g.rc, g.ny) : 0;
+    int cz = g.dim >= 3 ? cell_coord(r0aos[(size_t)i * 3 + 2], g.lo2, g.rc, g.nz) : 0;
+    int c = cx + g.nx * (cy + g.ny * cz);
+    cell[i] = c;
+    atomicAdd(&count[c], 1);
+}
+
+// exclusive scan over int counts, three kernels: per-block scan (1024
+// elements, 512 threads), scan of block totals (one block, sequential
+// chunks), add block offsets.
+constexpr int kScanBlock = 1024;
+
+__global__ void k_scan_local(const int* __restrict__ in, int* __restrict__ out, int count,
+                             int* __restrict__ totals)
+{
+    __shared__ int s[kScanBlock];
+    int base = blockIdx.x * kScanBlock;
+    for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x)
+        s[k] = base + k < count ? in[base + k] : 0;
+    __syncthreads();
+    // Hillis-Steele inclusive scan
+    for (int off = 1; off < kScanBlock; off <<= 1) {
+        int vals[2];
+        for (int q = 0; q < 2; ++q) {
+            int k = threadIdx.x + q * blockDim.x;
+            vals[q] = k >= off ? s[k - off] : 0;
+        }
+        __syncthreads();
+        for (int q = 0; q < 2; ++q) s[threadIdx.x + q * blockDim.x] += vals[q];
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < kScanBlock; k += blockDim.x)
+        if (base + k < count) out[base + k] = k == 0 ? 0 : s[k - 1];
+    if (threadIdx.x == 0) totals[blockIdx.x] = s[kScanBlock - 1];
+}
+
+__global__ void k_scan_totals(int* __restrict__ totals, int nb, int* __restrict__ grand)
+{
+    if (threadIdx.x != 0) return;
+    long long run = 0;
+    for (int b = 0; b < nb; ++b) {
+        long long t = totals[b];
+        totals[b] = (int)run;
+        run += t;
+    }
+    *grand = run > 0x7fffffffLL ? -1 : (int)run;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int count, const int* __restrict__ totals,
+                           const int* __restrict__ grand)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) out[k] += totals[k / kScanBlock];
+    if (k == 0) out[count] = *grand;
+}
+
+__global__ void k_scatter(const int* __restrict__ cell, int n, const int* __restrict__ start,
+                          int* __restrict__ fill, int* __restrict__ perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell[i];
+    perm[start[c] + atomicAdd(&fill[c], 1)] = i;
+}
+
+// stable order inside each cell: ascending original id (insertion sort)
+__global__ void k_cell_sort(const int* __restrict__ start, int ncells, int* __restrict__ perm)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int a = start[c], b = start[c + 1];
+    for (int k = a + 1; k < b; ++k) {
+        int x = perm[k];
+        int m = k - 1;
+        while (m >= a && perm[m] > x) {
+            perm[m + 1] = perm[m];
+            --m;
+        }
+        perm[m + 1] = x;
+    }
+}
+
+template <typename T>
+__global__ void k_gather(const int* __restrict__ perm, int n, const double* __restrict__ r0aos,
+                         const double* __restrict__ vol, double vol0, const uint8_t* __restrict__ fl,
+                         const double* __restrict__ u0, const int* __restrict__ cell_orig,
+                         double rho0, int* __restrict__ inv, int* __restrict__ cell_of,
+                         double* __restrict__ r0, uint8_t* __restrict__ flags, T* __restrict__ mass,
+                         double* __restrict__ u, float* __restrict__ uhi, float* __restrict__ ulo)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int i = perm[s];
+    inv[i] = s;
+    cell_of[s] = cell_orig[i];
+    for (int a = 0; a < 3; ++a) r0[(size_t)a * n + s] = r0aos[(size_t)i * 3 + a];
+    flags[s] = fl ? fl[i] : 0;
+    mass[s] = (T)(rho0 * (vol ? vol[i] : vol0));
+    // u at the half step, AoS padded to 4: FP64 [n][4] or FP32 hi/lo [n][4]
+    for (int a = 0; a < 4; ++a) {
+        double x = (u0 && a < 3) ? u0[(size_t)i * 3 + a] : 0.0;
+        if (u) u[(size_t)s * 4 + a] = x;
+        if (uhi) {
+            float hi = (float)x;
+            uhi[(size_t)s * 4 + a] = hi;
+            ulo[(size_t)s * 4 + a] = (float)(x - (double)hi);
+        }
+    }
+}
+
+// colour = sum_a (i_a mod 3) 3^a, per non-empty cell
+__device__ inline int cell_colour(int c, int dim, int nx, int ny)
+{
+    int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    int col = cx % 3;
+    if (dim >= 2) col += 3 * (cy % 3);
+    if (dim >= 3) col += 9 * (cz % 3);
+    return col;
+}
+
+__global__ void k_colour_count(const int* __restrict__ start, int ncells, int dim, int nx, int ny,
+                               int* __restrict__ ccount)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    if (start[c + 1] == start[c]) return;
+    atomicAdd(&ccount[cell_colour(c, dim, nx, ny)], 1);
+}
+
+__global__ void k_colour_fill(const int* __restrict__ start, int ncells, int dim, int nx, int ny,
+                              const int* __restrict__ cptr, int* __restrict__ cfill,
+                              int* __restrict__ ccells)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    if (start[c + 1] == start[c]) return;
+    int col = cell_colour(c, dim, nx, ny);
+    ccells[cptr[col] + atomicAdd(&cfill[col], 1)] = c;
+}
+
+// The 3^d-cell footprint of a cell is at most 9 runs of consecutive cells
+// (x-neighbours are consecutive ids), each a contiguous range of sorted
+// particles.  Calls f(range_begin, range_end, offset_in_footprint).
+template <typename F>
+__device__ inline int for_footprint(int c, int dim, int nx, int ny, int nz,
+                                    const int* __restrict__ start, F f)
+{
+    int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    int xlo = max(cx - 1, 0), xhi = min(cx + 1, nx - 1);
+    int ylo = dim >= 2 ? max(cy - 1, 0) : 0, yhi = dim >= 2 ? min(cy + 1, ny - 1) : 0;
+    int zlo = dim >= 3 ? max(cz - 1, 0) : 0, zhi = dim >= 3 ? min(cz + 1, nz - 1) : 0;
+    int off = 0;
+    for (int z = zlo; z <= zhi; ++z)
+        for (int y = ylo; y <= yhi; ++y) {
+            int c0 = xlo + nx * (y + ny * z), c1 = xhi + nx * (y + ny * z);
+            int a = start[c0], b = start[c1 + 1];
+            f(a, b, off);
+            off += b - a;
+        }
+    return off;
+}
+
+__global__ void k_csr_count(const double* __restrict__ r0, int n, int dim, int nx, int ny, int nz,
+                            const int* __restrict__ start, const int* __restrict__ cell_of,
+                            double rc2, int* __restrict__ deg)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cnt = 0;
+    for_footprint(cell_of[i], dim, nx, ny, nz, start, [&](int a, int b, int) {
+        for (int j = a; j < b; ++j) {
+            if (j == i) continue;
+            double d2 = dist2(dim, r0, n, i, j);
+            if (d2 > 0.0 && d2 < rc2) ++cnt;
+        }
+    });
+    deg[i] = cnt;
+}
+
+// neighbours (ascending original id), footprint-local index, damping weight
+// w_ij = V_i V_j W'(r)/r, and per particle: sum w, sum w^2, G_i = sum_j V_j
+// grad0_i W_ij, and B0_i = (-sum_j V_j r0_ij (x) grad0_i W_ij)^-1 (in FP64).
+template <typename T>
+__global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx, int ny, int nz,
+                           const int* __restrict__ start, const int* __restrict__ cell_of,
+                           double rc2, double h, double rho0, const T* __restrict__ mass,
+                           const int* __restrict__ row_ptr, int* __restrict__ col,
+                           uint16_t* __restrict__ loc, T* __restrict__ w, T* __restrict__ sumw,
+                           T* __restrict__ sumw2, T* __restrict__ Gs, T* __restrict__ B0,
+                           const int* __restrict__ perm, DevScalars* sc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = row_ptr[i];
+    double Vi = (double)mass[i] / rho0;
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double G[3] = {0, 0, 0};
+    double sw = 0.0, sw2 = 0.0;
+    for_footprint(cell_of[i], dim, nx, ny, nz, start, [&](int a, int b, int off) {
+        for (int j = a; j < b; ++j) {
+            if (j == i) continue;
+            double d2 = dist2(dim, r0, n, i, j);
+            if (!(d2 > 0.0 && d2 < rc2)) continue;
+            double r = sqrt(d2);
+            double f = wendland_dw_over_r(dim, h, r);
+            double Vj = (double)mass[j] / rho0;
+            double x[3] = {0, 0, 0};
+            for (int q = 0; q < dim; ++q) x[q] = r0[(size_t)q * n + i] - r0[(size_t)q * n + j];
+            for (int p = 0; p < dim; ++p) {
+                G[p] += Vj * f * x[p];
+                for (int q = 0; q < dim; ++q) M[p][q] -= Vj * f * x[p] * x[q];
+            }
+            double wij = Vi * Vj * f;
+            sw += wij;
+            sw2 += wij * wij;
+            col[k] = j;
+            loc[k] = (uint16_t)(off + (j - a));
+            w[k] = (T)wij;
+            ++k;
+        }
+    });
+    // Canonical neighbour order of a row: ascending ORIGINAL particle id.  The
+    // pairwise local operator applies its pair updates in row order (Sec. 3.2),
+    // so the order is part of the result; insertion sort by perm[col].
+    {
+        const int k0 = row_ptr[i];
+        for (int a = k0 + 1; a < k; ++a) {
+            int cj = col[a];
+            uint16_t lj = loc[a];
+            T wj = w[a];
+            int key = perm[cj];
+            int m = a - 1;
+            while (m >= k0 && perm[col[m]] > key) {
+                col[m + 1] = col[m];
+                loc[m + 1] = loc[m];
+                w[m + 1] = w[m];
+                --m;
+            }
+            col[m + 1] = cj;
+            loc[m + 1] = lj;
+            w[m + 1] = wj;
+        }
+    }
+    sumw[i] = (T)sw;
+    sumw2[i] = (T)sw2;
+    for (int p = 0; p < 3; ++p) Gs[(size_t)p * n + i] = (T)G[p];
+    double inv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double det;
+    if (dim == 2) {
+        det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+        inv[0][0] = M[1][1] / det;
+        inv[0][1] = -M[0][1] / det;
+        inv[1][0] = -M[1][0] / det;
+        inv[1][1] = M[0][0] / det;
+    } else {
+        double c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+        double c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+        double c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+        det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
+        inv[0][0] = c00 / det;
+        inv[1][0] = c01 / det;
+        inv[2][0] = c02 / det;
+        inv[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / det;
+        inv[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / det;
+        inv[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / det;
+        inv[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / det;
+        inv[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / det;
+        inv[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / det;
+    }
+    if (!(fabs(det) >= 1e-8)) {
+        if (atomicCAS(&sc->status, DEV_OK, DEV_SINGULAR_B0) == DEV_OK) sc->err_index = i;
+    }
+    for (int p = 0; p < dim; ++p)
+        for (int q = 0; q < dim; ++q) B0[(size_t)(p * dim + q) * n + i] = (T)inv[p][q];
+}
+
+__global__ void k_sell_width(const int* __restrict__ row_ptr, int n, int nslices,
+                             int* __restrict__ slots)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    int wmax = 0;
+    for (int l = 0; l < 32; ++l) {
+        int i = s * 32 + l;
+        if (i < n) wmax = max(wmax, row_ptr[i + 1] - row_ptr[i]);
+    }
+    slots[s] = wmax * 32;
+}
+
+template <typename T>
+__global__ void k_sell_fill(const double* __restrict__ r0, int n, int dim, double h, double rho0,
+                            const T* __restrict__ mass, const int* __restrict__ row_ptr,
+                            const int* __restrict__ col, const int* __restrict__ sell_ptr,
+                            int* __restrict__ scol, T* __restrict__ sg, int64_t nslots)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = i >> 5, lane = i & 31;
+    int base = sell_ptr[s], width = (sell_ptr[s + 1] - base) >> 5;
+    int k0 = row_ptr[i], deg = row_ptr[i + 1] - k0;
+    for (int t = 0; t < width; ++t) {
+        int64_t slot = (int64_t)base + t * 32 + lane;
+        double g[3] = {0, 0, 0};
+        int j = i;  // padding: self with zero weight contributes nothing
+        if (t < deg) {
+            j = col[k0 + t];
+            double x[3] = {0, 0, 0}, d2 = 0;
+            for (int q = 0; q < dim; ++q) {
+                x[q] = r0[(size_t)q * n + i] - r0[(size_t)q * n + j];
+                d2 += x[q] * x[q];
+            }
+            double f = wendland_dw_over_r(dim, h, sqrt(d2)) * (double)mass[j] / rho0;
+            for (int q = 0; q < dim; ++q) g[q] = f * x[q];
+        }
+        scol[slot] = j;
+        for (int q = 0; q < 3; ++q) sg[(size_t)q * nslots + slot] = (T)g[q];
+    }
+}
+
+__global__ void k_foot_stats(const int* __restrict__ start, int ncells, int dim, int nx, int ny,
+                             int nz, const int* __restrict__ row_ptr, int* __restrict__ out)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int a = start[c], b = start[c + 1];
+    if (a == b) return;
+    int foot = for_footprint(c, dim, nx, ny, nz, start, [](int, int, int) {});
+    atomicMax(&out[0], foot);
+    atomicMax(&out[1], row_ptr[b] - row_ptr[a]);
+    atomicMax(&out[2], b - a);
+}
+
+srdr_status scan_exclusive(const int* in, int* out, int count, int* tmp, cudaStream_t st)
+{
+    // tmp holds nb totals followed by 1 grand total
+    int nb = (count + kScanBlock - 1) / kScanBlock;
+    if (nb < 1) nb = 1;
+    k_scan_local<<<nb, kScanBlock / 2, 0, st>>>(in, out, count, tmp);
+    k_scan_totals<<<1, 32, 0, st>>>(tmp, nb, tmp + nb);
+    k_scan_add<<<nblocks(count + 1), kThreads, 0, st>>>(out, count, tmp, tmp + nb);
+    SRDR_CK(cudaGetLastError());
+    return SRDR_OK;
+}
+
+template <typename T>
+srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const double* vol_host,
+                        const uint8_t* flags_host, const double* u0_host)
+{
+    cudaStream_t st = b->stream;
+    int n = (int)n64;
+    int dim = b->dim;
+    // staging of the caller's arrays (original order)
+    double *r0aos = nullptr, *vol = nullptr, *u0 = nullptr;
+    uint8_t* fl = nullptr;
+    std::vector<double> r0pad((size_t)n * 3, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < dim; ++a) r0pad[(size_t)i * 3 + a] = r0_host[(size_t)i * 3 + a];
+    SRDR_TRY(dalloc(b, &r0aos, (size_t)n * 3));
+    SRDR_CK(cudaMemcpyAsync(r0aos, r0pad.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (vol_host) {
+        SRDR_TRY(dalloc(b, &vol, n));
+        SRDR_CK(cudaMemcpyAsync(vol, vol_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    }
+    if (flags_host) {
+        SRDR_TRY(dalloc(b, &fl, n));
+        SRDR_CK(cudaMemcpyAsync(fl, flags_host, n, cudaMemcpyHostToDevice, st));
+    }
+    std::vector<double> u0pad;
+    if (u0_host) {
+        u0pad.assign((size_t)n * 3, 0.0);
+        for (int64_t i = 0; i < n; ++i)
+            for (int a = 0; a < dim; ++a) u0pad[(size_t)i * 3 + a] = u0_host[(size_t)i * 3 + a];
+        SRDR_TRY(dalloc(b, &u0, (size_t)n * 3));
+        SRDR_CK(cudaMemcpyAsync(u0, u0pad.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    }
+
+    // bounding box -> cell grid
+    int nbb = std::min(nblocks(n), 1024);
+    double *bpart = nullptr, *bbox = nullptr;
+    SRDR_TRY(dalloc(b, &bpart, (size_t)nbb * 6));
+    SRDR_TRY(dalloc(b, &bbox, 6));
+    k_bbox_partial<<<nbb, kThreads, 0, st>>>(r0aos, n, bpart);
+    k_bbox_final<<<1, 32, 0, st>>>(bpart, nbb, bbox);
+    double hb[6];
+    SRDR_CK(cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) {
+        b->lo[a] = hb[a];
+        b->nc[a] = 1;
+        if (a < dim) {
+            double span = floor((hb[3 + a] - hb[a]) / b->rc);
+            if (!(span >= 0.0) || span > 1e8) {
+                set_error("body extent / cut-off out of range on axis %d", a);
+                return SRDR_ERR_INVALID;
+            }
+            b->nc[a] = (int)span + 1;
+        }
+        total *= b->nc[a];
+    }
+    if (total > (1 << 28)) {
+        set_error("too many cells (%lld): body too sparse for its cut-off", (long long)total);
+        return SRDR_ERR_INVALID;
+    }
+    b->ncells = (int)total;
+    int ncells = b->ncells;
+    Grid g{dim, b->nc[0], b->nc[1], b->nc[2], b->lo[0], b->lo[1], b->lo[2], b->rc};
+
+    int *cell_orig = nullptr, *count = nullptr, *fill = nullptr, *tmp = nullptr;
+    int ntmp = (std::max<int64_t>(ncells, n) + 1) / kScanBlock + 4;
+    SRDR_TRY(dalloc(b, &cell_orig, n));
+    SRDR_TRY(dalloc(b, &count, ncells));
+    SRDR_TRY(dalloc(b, &fill, ncells));
+    SRDR_TRY(dalloc(b, &tmp, ntmp));
+    SRDR_TRY(dalloc(b, &b->cell_start, (size_t)ncells + 1));
+    SRDR_TRY(dalloc(b, &b->perm, n));
+    SRDR_TRY(dalloc(b, &b->inv, n));
+    SRDR_TRY(dalloc(b, &b->cell_of, n));
+    SRDR_CK(cudaMemsetAsync(count, 0, sizeof(int) * ncells, st));
+    SRDR_CK(cudaMemsetAsync(fill, 0, sizeof(int) * ncells, st));
+    k_cell_hash<<<nblocks(n), kThreads, 0, st>>>(r0aos, n, g, cell_orig, count);
+    SRDR_TRY(scan_exclusive(count, b->cell_start, ncells, tmp, st));
+    k_scatter<<<nblocks(n), kThreads, 0, st>>>(cell_orig, n, b->cell_start, fill, b->perm);
+    k_cell_sort<<<nblocks(ncells), kThreads, 0, st>>>(b->cell_start, ncells, b->perm);
+
+    // sorted particle arrays and the initial (half-step) displacement
+    SRDR_TRY(dalloc(b, &b->r0, (size_t)n * 3));
+    SRDR_TRY(dalloc(b, &b->flags, n));
+    T* mass = nullptr;
+    SRDR_TRY(dalloc(b, &mass, n));
+    b->mass = mass;
+    if (b->prec == SRDR_FP64) {
+        SRDR_TRY(dalloc(b, &b->u, (size_t)n * 4));
+    } else {
+        SRDR_TRY(dalloc(b, &b->uhi, (size_t)n * 4));
+        SRDR_TRY(dalloc(b, &b->ulo, (size_t)n * 4));
+    }
+    k_gather<T><<<nblocks(n), kThreads, 0, st>>>(b->perm, n, r0aos, vol, b->vol0, fl, u0, cell_orig,
+                                                 b->desc.rho0, b->inv, b->cell_of, b->r0, b->flags,
+                                                 mass, b->u, b->uhi, b->ulo);
+    SRDR_CK(cudaGetLastError());
+
+    // colour split: non-empty cells grouped by colour
+    b->ncolours = dim == 2 ? 9 : 27;
+    int *ccount = nullptr, *cfill = nullptr, *cptr = nullptr;
+    SRDR_TRY(dalloc(b, &ccount, 27));
+    SRDR_TRY(dalloc(b, &cfill, 27));
+    SRDR_TRY(dalloc(b, &cptr, 28));
+    b->colour_ptr_d = cptr;
+    SRDR_CK(cudaMemsetAsync(ccount, 0, sizeof(int) * 27, st));
+    SRDR_CK(cudaMemsetAsync(cfill, 0, sizeof(int) * 27, st));
+    k_colour_count<<<nblocks(ncells), kThreads, 0, st>>>(b->cell_start, ncells, dim, g.nx, g.ny,
+                                                         ccount);
+    int hcount[27];
+    SRDR_CK(cudaMemcpyAsync(hcount, ccount, sizeof(hcount), cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    b->colour_ptr.assign(b->ncolours + 1, 0);
+    for (int c = 0; c < b->ncolours; ++c) b->colour_ptr[c + 1] = b->colour_ptr[c] + hcount[c];
+    b->ncells_nonempty = b->colour_ptr[b->ncolours];
+    SRDR_TRY(dalloc(b, &b->colour_cells, std::max(1, b->ncells_nonempty)));
+    SRDR_CK(cudaMemcpyAsync(cptr, b->colour_ptr.data(), sizeof(int) * (b->ncolours + 1),
+                            cudaMemcpyHostToDevice, st));
+    k_colour_fill<<<nblocks(ncells), kThreads, 0, st>>>(b->cell_start, ncells, dim, g.nx, g.ny,
+                                                        cptr, cfill, b->colour_cells);
+
+    // neighbour CSR
+    int* deg = nullptr;
+    SRDR_TRY(dalloc(b, &deg, n));
+    SRDR_TRY(dalloc(b, &b->row_ptr, (size_t)n + 1));
+    double rc2 = b->rc * b->rc;
+    k_csr_count<<<nblocks(n), kThreads, 0, st>>>(b->r0, n, dim, g.nx, g.ny, g.nz, b->cell_start,
+                                                 b->cell_of, rc2, deg);
+    SRDR_TRY(scan_exclusive(deg, b->row_ptr, n, tmp, st));
+    int nnz = 0;
+    SRDR_CK(cudaMemcpyAsync(&nnz, b->row_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    if (nnz < 0) {
+        set_error("more than 2^31 neighbour pairs");
+        return SRDR_ERR_INVALID;
+    }
+    b->nnz = nnz;
+    T *w = nullptr, *sumw = nullptr, *sumw2 = nullptr, *Gs = nullptr, *B0 = nullptr, *PB = nullptr;
+    SRDR_TRY(dalloc(b, &b->col, std::max(nnz, 1)));
+    SRDR_TRY(dalloc(b, &b->loc, std::max(nnz, 1)));
+    SRDR_TRY(dalloc(b, &w, std::max(nnz, 1)));
+    SRDR_TRY(dalloc(b, &sumw, n));
+    SRDR_TRY(dalloc(b, &sumw2, n));
+    SRDR_TRY(dalloc(b, &Gs, (size_t)n * 3));
+    SRDR_TRY(dalloc(b, &B0, (size_t)n * dim * dim));
+    b->pb_stride = pb_stride(sizeof(T), dim);
+    SRDR_TRY(dalloc(b, &PB, (size_t)n * b->pb_stride));
+    b->w = w;
+    b->sumw = sumw;
+    b->sumw2 = sumw2;
+    b->Gs = Gs;
+    b->B0 = B0;
+    b->PB = PB;
+    SRDR_CK(cudaMemsetAsync(PB, 0, sizeof(T) * (size_t)n * b->pb_stride, st));
+    k_csr_fill<T><<<nblocks(n), kThreads, 0, st>>>(b->r0, n, dim, g.nx, g.ny, g.nz, b->cell_start,
+                                                   b->cell_of, rc2, b->h, b->desc.rho0, mass,
+                                                   b->row_ptr, b->col, b->loc, w, sumw, sumw2, Gs,
+                                                   B0, b->perm, b->sc);
+    SRDR_CK(cudaGetLastError());
+
+    // sliced ELL for the passes
+    b->nslices = (n + 31) / 32;
+    int* slots = nullptr;
+    SRDR_TRY(dalloc(b, &slots, b->nslices));
+    SRDR_TRY(dalloc(b, &b->sell_ptr, (size_t)b->nslices + 1));
+    k_sell_width<<<nblocks(b->nslices), kThreads, 0, st>>>(b->row_ptr, n, b->nslices, slots);
+    SRDR_TRY(scan_exclusive(slots, b->sell_ptr, b->nslices, tmp, st));
+    int nslots = 0;
+    SRDR_CK(cudaMemcpyAsync(&nslots, b->sell_ptr + b->nslices, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    if (nslots < 0) {
+        set_error("sliced-ELL layout exceeds 2^31 slots");
+        return SRDR_ERR_INVALID;
+    }
+    b->nslots = nslots;
+    T* sg = nullptr;
+    SRDR_TRY(dalloc(b, &b->sell_col, std::max(nslots, 1)));
+    SRDR_TRY(dalloc(b, &sg, (size_t)std::max(nslots, 1) * 3));
+    b->sell_g = sg;
+    k_sell_fill<T><<<nblocks(n), kThreads, 0, st>>>(b->r0, n, dim, b->h, b->desc.rho0, mass,
+                                                    b->row_ptr, b->col, b->sell_ptr, b->sell_col,
+                                                    sg, std::max(nslots, 1));
+
+    // footprint maxima size the damping sweep's shared memory
+    int* fs = nullptr;
+    SRDR_TRY(dalloc(b, &fs, 3));
+    SRDR_CK(cudaMemsetAsync(fs, 0, sizeof(int) * 3, st));
+    k_foot_stats<<<nblocks(ncells), kThreads, 0, st>>>(b->cell_start, ncells, dim, g.nx, g.ny, g.nz,
+                                                       b->row_ptr, fs);
+    int hfs[3];
+    SRDR_CK(cudaMemcpyAsync(hfs, fs, sizeof(hfs), cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    SRDR_CK(cudaGetLastError());
+    b->max_foot = hfs[0];
+    b->max_pairs = hfs[1];
+    b->max_cell = hfs[2];
+    SRDR_TRY(dalloc(b, &b->bar, 2));
+    SRDR_CK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * 2, st));
+    if (b->max_foot >= 65536) {
+        set_error("a cell footprint holds %d particles (limit 65535)", b->max_foot);
+        return SRDR_ERR_INVALID;
+    }
+    // velocity state and KE partials
+    T* v = nullptr;
+    SRDR_TRY(dalloc(b, &v, (size_t)n * 3));
+    b->v = v;
+    SRDR_CK(cudaMemsetAsync(v, 0, sizeof(T) * (size_t)n * 3, st));
+    b->ke_blocks = nblocks(n);
+    SRDR_TRY(dalloc(b, &b->ke_part, b->ke_blocks));
+    SRDR_CK(cudaMemsetAsync(b->ke_part, 0, sizeof(double) * b->ke_blocks, st));
+
+    // release the staging buffers
+    SRDR_CK(cudaStreamSynchronize(st));
+    for (void* p : {(void*)r0aos, (void*)vol, (void*)u0, (void*)fl, (void*)bpart, (void*)bbox,
+                    (void*)cell_orig, (void*)count, (void*)fill, (void*)ccount, (void*)cfill,
+                    (void*)deg, (void*)slots, (void*)fs, (void*)tmp})
+        SRDR_TRY(dev_free(b, p));
+    SRDR_CK(cudaStreamSynchronize(st));
+    if (b->sc_host) {
+        SRDR_CK(cudaMemcpy(b->sc_host, b->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+        if (b->sc_host->status == DEV_SINGULAR_B0) {
+            set_error("singular correction matrix at particle (sorted index) %lld",
+                      (long long)b->sc_host->err_index);
+            return SRDR_ERR_INVALID;
+        }
+    }
+    return SRDR_OK;
+}
+
+}  // namespace
+
+srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* vol,
+                       const uint8_t* flags, const double* u0)
+{
+    if (n < 1 || n > 0x7fffffffLL / 3) {
+        set_error("particle count %lld out of range", (long long)n);
+        return SRDR_ERR_INVALID;
+    }
+    b->n = n;
+    if (b->prec == SRDR_FP64) return build_typed<double>(b, n, r0, vol, flags, u0);
+    return build_typed<float>(b, n, r0, vol, flags, u0);
+}
+
+}  // namespace srdr

@@ -1,0 +1,256 @@
+// srdr_internal.cuh — internal types and device helpers of the srdr library
+// (splitting random-choice dynamic relaxation for TL-SPH, arXiv 2103.08932).
+//
+// Data layout in HBM (all per-particle arrays in SORTED order: particles
+// sorted by (cell id, original id), the canonical order of the splitting
+// cell-linked list):
+//   r0    FP64 [3][n] SoA reference positions
+//   u     FP64 [n][4] (FP64 mode) or FP32 hi and lo arrays [n][4] (FP32 mode,
+//         u = hi + lo), held at the half step u^{n+1/2}; AoS so that one
+//         neighbour gather is one or two 16-byte loads
+//   v     T [3][n]
+//   B0    T [D*D][n] row-major tensor components, SoA (read by the owner only)
+//   PB    T [n][pb_stride] AoS padded to 16-byte vectors (gathered)
+//   G     T [3][n]   sum_j V_j grad W_ij (for the difference form of the force)
+//   CSR   row_ptr int32 [n+1], col int32 [nnz] (sorted ids, ascending),
+//         loc uint16 [nnz] (index of j inside the 3^d-cell footprint of
+//         cell(i)), w T [nnz] = V_i V_j W'(r)/r  (damping sweep)
+//   SELL  32-row slices: sell_ptr int32 [nslices+1], sell_col int32 [slots],
+//         sell_g T [3][slots] = V_j grad0_i W_ij  (stress and force passes)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/srdr.h"
+
+namespace srdr {
+
+void set_error(const char* fmt, ...);
+
+#define SRDR_CK(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ::srdr::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                              __LINE__);                                                   \
+            return SRDR_ERR_CUDA;                                                          \
+        }                                                                                  \
+    } while (0)
+
+#define SRDR_TRY(call)                         \
+    do {                                       \
+        srdr_status s_ = (call);               \
+        if (s_ != SRDR_OK) return s_;          \
+    } while (0)
+
+// device-side scalars of one body, updated by the kernels
+struct DevScalars {
+    double ke;
+    double ke_max;
+    double tol;            // relax criterion (0: never done)
+    long long step;        // steps completed
+    long long damped;      // damped steps completed
+    int done;              // criterion met or error: later step kernels skip
+    int status;            // 0, or a device error code (SRDR_ERR_*)
+    long long err_index;   // first offending particle / cell for status
+};
+
+// device error codes written to DevScalars::status
+enum { DEV_OK = 0, DEV_SINGULAR_B0 = 1, DEV_NONFINITE = 2, DEV_TIMEOUT = 3 };
+
+template <typename T>
+struct StepArgs {
+    int n;
+    const int* __restrict__ sell_ptr;
+    const int* __restrict__ sell_col;
+    const T* __restrict__ g0;
+    const T* __restrict__ g1;
+    const T* __restrict__ g2;
+    const T* __restrict__ B0;   // [D*D][n]
+    T* __restrict__ PB;         // [D*D][n]
+    const T* __restrict__ Gs;   // [3][n]
+    T* __restrict__ v;          // [3][n]
+    double* __restrict__ u;     // [3][n] FP64 mode
+    float* __restrict__ uhi;    // [3][n] FP32 mode
+    float* __restrict__ ulo;    // [3][n] FP32 mode
+    const uint8_t* __restrict__ flags;
+    const T* __restrict__ mass;
+    double* __restrict__ ke_part;
+    DevScalars* sc;
+    T lambda, mu, inv_rho0, dt;
+    T grav[3];
+    T endl[3];
+};
+
+template <typename T>
+struct SweepArgs {
+    int n;
+    int dim;
+    int nx, ny, nz;
+    const int* __restrict__ cell_start;
+    const int* __restrict__ colour_cells;  // cells of this colour
+    int ncells_colour;
+    const int* __restrict__ row_ptr;
+    const uint16_t* __restrict__ loc;
+    const T* __restrict__ w;
+    const T* __restrict__ mass;
+    const T* __restrict__ sumw;
+    const T* __restrict__ sumw2;
+    T* __restrict__ v;
+    DevScalars* sc;
+    T c;          // 2 eta~ dt_loc, so that B_j = c w_ij
+    int backward;
+    int pairwise;
+    int max_foot;
+    int max_pairs;
+    int max_cell;
+};
+
+}  // namespace srdr
+
+// ---------------------------------------------------------------- the body
+struct srdr_body {
+    srdr_body_desc desc;
+    int dim = 3;
+    int prec = SRDR_FP64;
+    int64_t n = 0, nnz = 0;
+    int nc[3] = {1, 1, 1};
+    int ncells = 0, ncells_nonempty = 0, ncolours = 0;
+    cudaStream_t stream = nullptr;
+    double h = 0, rc = 0, lambda = 0, mu = 0, eta = 0, dt = 0, vol0 = 0;
+    double lo[3] = {0, 0, 0};
+
+    // device arrays
+    int* perm = nullptr;        // sorted -> original
+    int* inv = nullptr;         // original -> sorted
+    int* cell_start = nullptr;  // [ncells+1]
+    int* cell_of = nullptr;     // [n] cell id, sorted order
+    int* colour_cells = nullptr;
+    std::vector<int> colour_ptr;  // host [ncolours+1]
+    double* r0 = nullptr;       // [3][n]
+    uint8_t* flags = nullptr;   // [n]
+    void* mass = nullptr;       // T [n]
+    int* row_ptr = nullptr;
+    int* col = nullptr;
+    uint16_t* loc = nullptr;
+    void* w = nullptr;          // T [nnz]
+    int nslices = 0;
+    int64_t nslots = 0;
+    int* sell_ptr = nullptr;
+    int* sell_col = nullptr;
+    void* sell_g = nullptr;     // T [3][nslots]
+    void* B0 = nullptr;         // T [D*D][n]
+    void* PB = nullptr;
+    void* Gs = nullptr;         // T [3][n]
+    void* sumw = nullptr;
+    void* sumw2 = nullptr;
+    void* v = nullptr;          // T [3][n]
+    double* u = nullptr;        // FP64 [3][n]
+    float* uhi = nullptr;
+    float* ulo = nullptr;
+    double* ke_part = nullptr;
+    int ke_blocks = 0;
+    srdr::DevScalars* sc = nullptr;
+    srdr::DevScalars* sc_host = nullptr;  // pinned mirror
+
+    int pb_stride = 0;               // T elements per particle in PB
+    int max_foot = 0, max_pairs = 0, max_cell = 0;  // per-cell maxima
+    int* colour_ptr_d = nullptr;     // device copy of colour_ptr
+    unsigned* bar = nullptr;         // grid-barrier count and generation
+    int sweep_grid = 0;              // co-resident blocks of the sweep kernel
+    int sweep_smem = 0;
+
+    // host mirrors
+    int64_t step = 0;
+    int converged = 0;
+    int64_t launches = 0;
+
+    // kernel-class timing (CUDA events on the body stream)
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
+    size_t ev_next = 0;
+    int64_t k_launch[SRDR_K_NCLASS] = {0, 0, 0, 0, 0};
+
+    std::vector<void*> allocs;
+};
+
+namespace srdr {
+
+srdr_status dev_alloc(srdr_body* b, void** p, size_t bytes);
+srdr_status dev_free(srdr_body* b, void* p);
+template <typename P>
+inline srdr_status dalloc(srdr_body* b, P** p, size_t count)
+{
+    return dev_alloc(b, reinterpret_cast<void**>(p), count * sizeof(P));
+}
+
+// elements per particle of the AoS P B0 array (whole 16-byte vectors)
+inline int pb_stride(size_t tsize, int dim)
+{
+    if (dim == 2) return 4;
+    return tsize == 4 ? 12 : 10;
+}
+
+// setup (setup.cu)
+srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* vol,
+                       const uint8_t* flags, const double* u0);
+// kernel-class timing (api.cu): begin/end an interval of class k
+void prof_begin(srdr_body* b, int k, cudaEvent_t* ev);
+void prof_end(srdr_body* b, int k, cudaEvent_t ev);
+// stepping (step.cu)
+srdr_status launch_steps(srdr_body* b, int64_t nsteps);
+srdr_status sync_scalars(const srdr_body* b);
+srdr_status reset_scalars(srdr_body* b, double tol);
+
+// ------------------------------------------------------------ Philox4x64-10
+// Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11).  Round: (hi0,lo0) = M0*x0, (hi1,lo1) = M1*x2,
+// x <- (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0); key += Weyl constants
+// between rounds.
+__host__ __device__ inline uint64_t mul_hi64(uint64_t a, uint64_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+#endif
+}
+
+__host__ __device__ inline void philox4x64_10(const uint64_t c[4], const uint64_t k[2],
+                                              uint64_t out[4])
+{
+    uint64_t x0 = c[0], x1 = c[1], x2 = c[2], x3 = c[3];
+    uint64_t k0 = k[0], k1 = k[1];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
+        uint64_t h0 = mul_hi64(m0, x0), l0 = m0 * x0;
+        uint64_t h1 = mul_hi64(m1, x2), l1 = m1 * x2;
+        uint64_t y0 = h1 ^ x1 ^ k0, y2 = h0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = l1;
+        x2 = y2;
+        x3 = l0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+}
+
+// phi_n of the random choice: one draw per step from word 0
+__host__ __device__ inline double random_phi(uint64_t seed, uint64_t step)
+{
+    uint64_t c[4] = {step, 0, 0, 0}, k[2] = {seed, 0}, o[4];
+    philox4x64_10(c, k, o);
+    return (double)(o[0] >> 11) * 0x1.0p-53;
+}
+
+}  // namespace srdr

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle.
+
+Integer and index work (cells, colours, sweep order, neighbour lists) must be
+bit-exact.  Floating point: FP64 mode within 1e-9 relative after a few steps
+and within the stated 1e-5 relative per-step velocity error over 100 steps of
+the 2D cantilever; FP32-mixed mode within the bounds derived in the tests.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2103_08932_gb300 import srdr
+from paper_2103_08932_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2103_08932_gb300 import build
+    build.build()
+    srdr.lib()
+
+
+def oracle_for(spec, r0=None, flags=None, u0=None, damping=O.DAMP_PARTICLE, dt=0.0, **kw):
+    if r0 is None:
+        r0, flags, u0 = S.lattice(spec)
+    p = O.Params(dim=spec.dim, material=spec.material, rho0=spec.rho0, E=spec.E, nu=spec.nu,
+                 h=spec.h, gravity=spec.gravity, end_load=spec.end_load, beta=spec.beta,
+                 L_char=spec.L_char, alpha=spec.alpha, seed=spec.seed, damping=damping, dt=dt)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    has_u0 = u0 is not None and np.abs(u0).max() > 0
+    return O.OracleBody(p, r0[:, :spec.dim], vol_default=spec.vol, flags=flags,
+                        u0=u0[:, :spec.dim] if has_u0 else None)
+
+
+def gpu_for(spec, precision=srdr.SRDR_FP64, damping=srdr.SRDR_DAMP_PARTICLE, particles=None,
+            dt=0.0):
+    d = srdr.make_desc(spec, precision=precision, damping=damping, dt=dt)
+    if particles is None:
+        return srdr.Body(d)
+    r0, flags, u0 = particles
+    return srdr.Body(d, r0=r0, flags=flags, u0=u0)
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+SMALL3D = S.BodySpec(dim=3, extent=(0.021, 0.007, 0.009), dp=1e-3, clamp_axis=0, clamp_layers=3,
+                     material=S.NEO_HOOKEAN, E=2e6, nu=0.3, gravity=(0.0, -9.81, 0.0), beta=0.2,
+                     L_char=0.007, alpha=0.5, seed=2)
+SMALL2D = S.BodySpec(dim=2, extent=(0.05, 0.01, 0.0), dp=1e-3, clamp_axis=0, clamp_layers=3,
+                     material=S.SVK, E=2e6, nu=0.3, gravity=(0.0, -9.81, 0.0), beta=0.2,
+                     L_char=0.01, alpha=0.5, seed=0)
+
+
+# ------------------------------------------------------------------ integer parity
+@pytest.mark.parametrize("spec,jit", [(SMALL2D, 0.0), (SMALL2D, 0.3), (SMALL3D, 0.0), (SMALL3D, 0.35)])
+def test_cells_colours_order_neighbours_bit_exact(spec, jit):
+    if jit > 0:
+        parts = S.jittered(spec, jit, 17)
+    else:
+        parts = S.lattice(spec)
+    r0, flags, u0 = parts
+    ob = oracle_for(spec, r0, flags, u0)
+    gb = gpu_for(spec, particles=parts)
+    assert gb.n == ob.n and gb.nnz == ob.nnz
+    oc, ocol, oorder = ob.cells()
+    gc, gcol, gorder = gb.cells()
+    assert np.array_equal(oc, gc)
+    assert np.array_equal(ocol, gcol)
+    assert np.array_equal(oorder, gorder)
+    orow, ocolidx = ob.neighbours()
+    grow, gcolidx = gb.neighbours()
+    assert np.array_equal(orow, grow)
+    assert np.array_equal(ocolidx, gcolidx)
+
+
+def test_lattice_builder_matches_generator():
+    spec = S.compression_block_3d(dp=1e-3, edge=0.012)
+    gb = gpu_for(spec)
+    r0, flags, u0 = S.lattice(spec)
+    ob = oracle_for(spec, r0, flags, u0)
+    assert gb.n == len(r0)
+    # same particles, order and initial displacement as the generator
+    assert np.array_equal(gb.displacement(), u0)
+    oc, _, _ = ob.cells()
+    gc, _, _ = gb.cells()
+    assert np.array_equal(oc, gc)
+
+
+# ------------------------------------------------------------------ FP64 parity
+@pytest.mark.parametrize("spec", [SMALL2D, SMALL3D])
+def test_correction_matrix_fp64(spec):
+    ob = oracle_for(spec)
+    gb = gpu_for(spec)
+    assert rel(gb.field(srdr.SRDR_FIELD_B0), ob.get(O.B0)) < 1e-12
+
+
+@pytest.mark.parametrize("material", [S.SVK, S.NEO_HOOKEAN])
+@pytest.mark.parametrize("base", [SMALL2D, SMALL3D])
+def test_first_steps_fp64(material, base):
+    from dataclasses import replace
+    spec = replace(base, material=material)
+    ob = oracle_for(spec)
+    gb = gpu_for(spec)
+    for _ in range(6):
+        ob.step(1)
+        gb.step(1)
+        assert rel(gb.velocity(), ob.v) < 1e-9
+    assert rel(gb.field(srdr.SRDR_FIELD_PB), ob.get(O.PB)) < 1e-9
+    assert rel(gb.displacement(), ob.u) < 1e-9
+    st = gb.stats()
+    assert st["damped_steps"] == ob.damped_steps > 0
+    assert abs(st["ke"] - ob.ke) <= 1e-9 * ob.ke
+
+
+@pytest.mark.parametrize("material", [S.SVK, S.NEO_HOOKEAN])
+def test_cantilever_2d_100_steps_per_step_velocity(material):
+    """2D cantilever under gravity (L = 0.2 m, H = 0.02 m, dp = H/10, FP64):
+    max_i |v_gpu - v_oracle| / max_i |v_oracle| <= 1e-5 at each of 100 steps."""
+    spec = S.cantilever_2d(material)
+    ob = oracle_for(spec)
+    gb = gpu_for(spec)
+    worst = 0.0
+    for _ in range(100):
+        ob.step(1)
+        gb.step(1)
+        worst = max(worst, rel(gb.velocity(), ob.v))
+    assert ob.damped_steps == gb.stats()["damped_steps"] > 0
+    assert worst <= 1e-5
+    assert worst <= 1e-10  # FP64 against FP64: rounding order only
+
+
+@pytest.mark.parametrize("base", [SMALL2D, SMALL3D])
+def test_pairwise_scheme_fp64(base):
+    ob = oracle_for(base, damping=O.DAMP_PAIRWISE)
+    gb = gpu_for(base, damping=srdr.SRDR_DAMP_PAIRWISE)
+    ob.step(8)
+    gb.step(8)
+    assert ob.damped_steps > 0
+    assert rel(gb.velocity(), ob.v) < 1e-9
+
+
+def test_jittered_ragged_body_fp64():
+    # irregular spacing, a particle count that is not a multiple of 32
+    spec = S.BodySpec(dim=3, extent=(0.013, 0.005, 0.007), dp=1e-3, clamp_axis=0, clamp_layers=2,
+                      material=S.NEO_HOOKEAN, gravity=(0.0, -9.81, 3.0), beta=0.2, L_char=0.005,
+                      alpha=0.5, seed=1)
+    parts = S.jittered(spec, 0.3, 5)
+    assert len(parts[0]) % 32 != 0
+    ob = oracle_for(spec, *parts)
+    gb = gpu_for(spec, particles=parts)
+    ob.step(10)
+    gb.step(10)
+    assert ob.damped_steps > 0
+    assert rel(gb.velocity(), ob.v) < 1e-9
+    assert rel(gb.displacement(), ob.u) < 1e-9
+
+
+def test_prescribed_displacement_fp64():
+    spec = S.compression_block_3d(dp=1e-3, edge=0.01)
+    ob = oracle_for(spec, f_form=O.F_DISPLACEMENT)
+    gb = gpu_for(spec)
+    ob.step(5)
+    gb.step(5)
+    assert rel(gb.velocity(), ob.v) < 1e-9
+    u = gb.displacement()
+    assert rel(u, ob.u) < 1e-9
+    r0, flags, u0 = S.lattice(spec)
+    fixed = (flags & S.FLAG_CONSTRAINED) > 0
+    assert np.array_equal(u[fixed], u0[fixed])
+
+
+def test_end_load():
+    spec = S.BodySpec(dim=3, extent=(0.02, 0.005, 0.005), dp=1e-3, clamp_axis=0, clamp_layers=3,
+                      end_load_layer=True, end_load=(0.0, -40.0, 0.0), gravity=(0.0, 0.0, 0.0),
+                      material=S.NEO_HOOKEAN, beta=0.2, L_char=0.005, alpha=0.2, seed=0)
+    ob = oracle_for(spec)
+    gb = gpu_for(spec)
+    assert abs(gb.dt - ob.dt) <= 1e-15 * ob.dt
+    ob.step(5)
+    gb.step(5)
+    assert rel(gb.velocity(), ob.v) < 1e-9
+
+
+# ------------------------------------------------------------------ properties at any size
+def test_device_sweep_conserves_momentum():
+    """Zero stress (u = 0), no gravity, no constraints: a damped step changes v
+    only through S_d, which conserves sum m v exactly (Sec. 3.1)."""
+    spec = S.BodySpec(dim=3, extent=(0.03, 0.01, 0.012), dp=1e-3, clamp_axis=-1,
+                      gravity=(0.0, 0.0, 0.0), beta=0.2, L_char=0.01, alpha=0.2, seed=0)
+    assert O.phi(0, 0) < 0.2  # step 0 is damped for seed 0
+    gb = gpu_for(spec)
+    rng = np.random.default_rng(3)
+    v0 = rng.normal(size=(gb.n, 3))
+    # u^n = -dt/2 v^n puts the half-step displacement u^{n+1/2} at exactly 0
+    gb.write_state(u=-0.5 * gb.dt * v0, v=v0, step_index=0, ke_max=0.0)
+    gb.step(1)
+    v1 = gb.velocity()
+    assert gb.stats()["damped_steps"] == 1
+    assert np.abs(v1 - v0).max() > 1e-3
+    assert np.abs(v1.sum(0) - v0.sum(0)).max() <= 1e-12 * np.abs(v0).sum()
+    assert (v1 ** 2).sum() < (v0 ** 2).sum()
+
+
+def test_fp64_runs_are_bit_identical():
+    a = gpu_for(SMALL3D)
+    b = gpu_for(SMALL3D)
+    a.step(12)
+    b.step(12)
+    assert np.array_equal(a.velocity(), b.velocity())
+    assert np.array_equal(a.displacement(), b.displacement())
+
+
+def test_checkpoint_resume_equals_straight_run():
+    a = gpu_for(SMALL3D)
+    a.step(9)
+    u, v, st = a.displacement(), a.velocity(), a.stats()
+    b = gpu_for(SMALL3D)
+    b.write_state(u=u, v=v, step_index=st["step"], ke_max=st["ke_max"])
+    a.step(7)
+    b.step(7)
+    assert rel(b.velocity(), a.velocity()) < 1e-12
+    assert rel(b.displacement(), a.displacement()) < 1e-12
+
+
+# ------------------------------------------------------------------ FP32 mixed precision
+@pytest.mark.parametrize("base", [SMALL2D, SMALL3D])
+def test_fp32_mixed_steps(base):
+    """FP32 neighbour sums: each of the ~k terms carries a relative rounding of
+    ~6e-8 and the stress and force sums are written without cancellation, so a
+    few steps stay within ~1e-5 relative of FP64."""
+    ob = oracle_for(base)
+    gb = gpu_for(base, precision=srdr.SRDR_FP32_MIXED)
+    ob.step(10)
+    gb.step(10)
+    assert ob.damped_steps > 0
+    assert rel(gb.velocity(), ob.v) < 2e-5
+    assert rel(gb.displacement(), ob.u) < 2e-5
+
+
+# ------------------------------------------------------------------ degenerate inputs
+def test_single_layer_body_is_rejected():
+    spec = S.BodySpec(dim=3, extent=(0.01, 0.001, 0.01), dp=1e-3, clamp_axis=-1)
+    with pytest.raises(srdr.SrdrError) as e:
+        gpu_for(spec)
+    assert e.value.status == srdr.SRDR_ERR_INVALID
+    assert "singular" in str(e.value)
+
+
+def test_empty_body_is_rejected():
+    spec = SMALL3D
+    with pytest.raises(srdr.SrdrError) as e:
+        gpu_for(spec, particles=(np.zeros((0, 3)), np.zeros(0, np.uint8), None))
+    assert e.value.status == srdr.SRDR_ERR_INVALID
+
+
+def test_undamped_and_zero_alpha():
+    from dataclasses import replace
+    spec = replace(SMALL3D, alpha=0.0)
+    ob = oracle_for(spec)
+    gb = gpu_for(spec)
+    ob.step(5)
+    gb.step(5)
+    assert ob.damped_steps == 0 and gb.stats()["damped_steps"] == 0
+    assert rel(gb.velocity(), ob.v) < 1e-9
