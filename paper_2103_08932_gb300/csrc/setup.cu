@@ -201,7 +201,7 @@ __global__ void k_gather(const int* __restrict__ perm, int n, const double* __re
                          const double* __restrict__ u0, const int* __restrict__ cell_orig,
                          double rho0, int* __restrict__ inv, int* __restrict__ cell_of,
                          double* __restrict__ r0, uint8_t* __restrict__ flags, T* __restrict__ mass,
-                         double* __restrict__ u, float* __restrict__ uhi, float* __restrict__ ulo)
+                         T* __restrict__ minv, double* __restrict__ u, float* __restrict__ uhi, float* __restrict__ ulo)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -210,7 +210,9 @@ __global__ void k_gather(const int* __restrict__ perm, int n, const double* __re
     cell_of[s] = cell_orig[i];
     for (int a = 0; a < 3; ++a) r0[(size_t)a * n + s] = r0aos[(size_t)i * 3 + a];
     flags[s] = fl ? fl[i] : 0;
-    mass[s] = (T)(rho0 * (vol ? vol[i] : vol0));
+    const double m = rho0 * (vol ? vol[i] : vol0);
+    mass[s] = (T)m;
+    minv[s] = (T)(1.0 / m);
     // u at the half step, AoS padded to 4: FP64 [n][4] or FP32 hi/lo [n][4]
     for (int a = 0; a < 4; ++a) {
         double x = (u0 && a < 3) ? u0[(size_t)i * 3 + a] : 0.0;
@@ -544,6 +546,9 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     T* mass = nullptr;
     SRDR_TRY(dalloc(b, &mass, n));
     b->mass = mass;
+    T* minv = nullptr;
+    SRDR_TRY(dalloc(b, &minv, n));
+    b->minv = minv;
     if (b->prec == SRDR_FP64) {
         SRDR_TRY(dalloc(b, &b->u, (size_t)n * 4));
     } else {
@@ -552,7 +557,7 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     }
     k_gather<T><<<nblocks(n), kThreads, 0, st>>>(b->perm, n, r0aos, vol, b->vol0, fl, u0, cell_orig,
                                                  b->desc.rho0, b->inv, b->cell_of, b->r0, b->flags,
-                                                 mass, b->u, b->uhi, b->ulo);
+                                                 mass, minv, b->u, b->uhi, b->ulo);
     SRDR_CK(cudaGetLastError());
 
     // colour split: non-empty cells grouped by colour

@@ -98,6 +98,7 @@ struct SweepArgs {
     const uint16_t* __restrict__ loc;
     const T* __restrict__ w;
     const T* __restrict__ mass;
+    const T* __restrict__ minv;
     const T* __restrict__ sumw;
     const T* __restrict__ sumw2;
     T* __restrict__ v;
@@ -134,6 +135,7 @@ struct srdr_body {
     double* r0 = nullptr;       // [3][n]
     uint8_t* flags = nullptr;   // [n]
     void* mass = nullptr;       // T [n]
+    void* minv = nullptr;       // T [n] 1 / mass
     int* row_ptr = nullptr;
     int* col = nullptr;
     uint16_t* loc = nullptr;

@@ -22,6 +22,7 @@ namespace srdr {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kUnroll = 4;  // sliced-ELL slots per batch of loads in the passes
 inline int nblocks(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
 // ------------------------------------------------------------------ layouts
@@ -265,21 +266,31 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(StepArgs<T> a)
     for (int p = 0; p < D; ++p)
 #pragma unroll
         for (int q = 0; q < D; ++q) G[p][q] = 0;
-    for (int t = 0; t < width; ++t) {
-        int k = base + t * 32 + lane;
-        int j = __ldg(a.sell_col + k);
-        T g[D];
-        g[0] = __ldg(a.g0 + k);
-        g[1] = __ldg(a.g1 + k);
-        if constexpr (D == 3) g[2] = __ldg(a.g2 + k);
-        T xj[3], lj[3];
-        UAcc<T>::load(a.u, a.uhi, a.ulo, j, xj, lj);
+    // slots in batches of kUnroll: all stream loads, then all gathers, then
+    // the arithmetic, so each batch costs two memory round trips
+    for (int t0 = 0; t0 < width; t0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
 #pragma unroll
-        for (int p = 0; p < D; ++p) {
-            T du = UAcc<T>::diff(xi, li, xj, lj, p);
-#pragma unroll
-            for (int q = 0; q < D; ++q) G[p][q] += du * g[q];
+        for (int u = 0; u < kUnroll; ++u) {
+            const int k = base + (t0 + u) * 32 + lane;
+            const bool in = t0 + u < width;
+            jj[u] = in ? __ldg(a.sell_col + k) : i;
+            gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
+            gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
+            if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
         }
+        T xj[kUnroll][3], lj[kUnroll][3];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) UAcc<T>::load(a.u, a.uhi, a.ulo, jj[u], xj[u], lj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int p = 0; p < D; ++p) {
+                T du = UAcc<T>::diff(xi, li, xj[u], lj[u], p);
+#pragma unroll
+                for (int q = 0; q < D; ++q) G[p][q] += du * gg[u][q];
+            }
     }
     T B[D][D], H[D][D], PB[D][D];
 #pragma unroll
@@ -381,19 +392,27 @@ __global__ void __launch_bounds__(kThreads) k_pass_b(StepArgs<T> a, int final_st
         T acc[D];
 #pragma unroll
         for (int p = 0; p < D; ++p) acc[p] = 0;
-        for (int t = 0; t < width; ++t) {
-            int k = base + t * 32 + lane;
-            int j = __ldg(a.sell_col + k);
-            T g[D];
-            g[0] = __ldg(a.g0 + k);
-            g[1] = __ldg(a.g1 + k);
-            if constexpr (D == 3) g[2] = __ldg(a.g2 + k);
-            T Pj[D][D];
-            PBL<T, D>::load(a.PB, j, Pj);
+        for (int t0 = 0; t0 < width; t0 += kUnroll) {
+            int jj[kUnroll];
+            T gg[kUnroll][D];
 #pragma unroll
-            for (int p = 0; p < D; ++p)
+            for (int u = 0; u < kUnroll; ++u) {
+                const int k = base + (t0 + u) * 32 + lane;
+                const bool in = t0 + u < width;
+                jj[u] = in ? __ldg(a.sell_col + k) : i;
+                gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
+                gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
+                if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
+            }
+            T Pj[kUnroll][D][D];
 #pragma unroll
-                for (int q = 0; q < D; ++q) acc[p] += (Pj[p][q] - Pi[p][q]) * g[q];
+            for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, jj[u], Pj[u]);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int p = 0; p < D; ++p)
+#pragma unroll
+                    for (int q = 0; q < D; ++q) acc[p] += (Pj[u][p][q] - Pi[p][q]) * gg[u][q];
         }
         T Gi[D];
 #pragma unroll
@@ -491,39 +510,54 @@ __device__ inline T warp_allsum(T x)
     return x;
 }
 
-template <typename F>
-__device__ inline int foot_runs(int c, int dim, int nx, int ny, int nz,
-                                const int* __restrict__ start, F f)
+// The <= 9 runs of a cell's footprint, known to every lane of the warp:
+// run r covers sorted particles [a[r], a[r] + off[r+1] - off[r]) and sits at
+// footprint-local offset off[r].
+struct FootRuns {
+    int nruns;
+    int total;
+    int a[9];
+    int off[10];
+    __device__ int particle(int q) const
+    {
+        int j = 0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+            if (r < nruns && q >= off[r]) j = a[r] + (q - off[r]);
+        return j;
+    }
+};
+
+__device__ inline FootRuns foot_runs_warp(int c, int dim, int nx, int ny, int nz,
+                                          const int* __restrict__ start, int lane)
 {
-    int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-    int xlo = max(cx - 1, 0), xhi = min(cx + 1, nx - 1);
-    int ylo = dim >= 2 ? max(cy - 1, 0) : 0, yhi = dim >= 2 ? min(cy + 1, ny - 1) : 0;
-    int zlo = dim >= 3 ? max(cz - 1, 0) : 0, zhi = dim >= 3 ? min(cz + 1, nz - 1) : 0;
-    int off = 0;
-    for (int z = zlo; z <= zhi; ++z)
-        for (int y = ylo; y <= yhi; ++y) {
-            int c0 = xlo + nx * (y + ny * z), c1 = xhi + nx * (y + ny * z);
-            int ra = __ldg(start + c0), rb = __ldg(start + c1 + 1);
-            f(ra, rb, off);
-            off += rb - ra;
-        }
-    return off;
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    const int xlo = max(cx - 1, 0), xhi = min(cx + 1, nx - 1);
+    const int ylo = dim >= 2 ? max(cy - 1, 0) : 0, yhi = dim >= 2 ? min(cy + 1, ny - 1) : 0;
+    const int zlo = dim >= 3 ? max(cz - 1, 0) : 0, zhi = dim >= 3 ? min(cz + 1, nz - 1) : 0;
+    const int ny_r = yhi - ylo + 1;
+    FootRuns f;
+    f.nruns = ny_r * (zhi - zlo + 1);
+    int ra = 0, len = 0;
+    if (lane < f.nruns) {
+        const int y = ylo + lane % ny_r, z = zlo + lane / ny_r;
+        const int c0 = xlo + nx * (y + ny * z), c1 = xhi + nx * (y + ny * z);
+        ra = __ldg(start + c0);
+        len = __ldg(start + c1 + 1) - ra;
+    }
+    int run = 0;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        f.a[r] = __shfl_sync(0xffffffffu, ra, r);
+        const int l = __shfl_sync(0xffffffffu, len, r);
+        f.off[r] = run;
+        run += r < f.nruns ? l : 0;
+    }
+    f.off[9] = run;
+    f.total = run;
+    return f;
 }
 
-// One warp per cell of the colour.  The cell's 3^d-cell footprint velocities,
-// inverse masses and the cell's CSR rows are staged in shared memory; the
-// cell's particles are then updated one after another (ascending forward,
-// descending backward), lanes spread over each particle's neighbours.
-// Same-colour footprints are disjoint (Sec. 3.4), so the cells of one colour
-// run concurrently without write conflicts and the result does not depend on
-// their order.
-//
-// Particle-by-particle local update D_i (Sec. 3.1), B_j = c w_ij:
-//   E_i = -sum_j B_j (v_i - v_j),  k = E_i / ((sum B - m_i)^2 + sum B^2)
-//   v_i <- v_i + (sum B - m_i) k
-//   v_j <- v_j - B_j (v_i^new - v_j + B_j k) / m_j   (v_j^n on the right)
-// Pairwise local update (Sec. 3.2): pairs (i, j) in row order then reverse,
-// each over half the local step, dv_i = m_j B v_ij / (m_i m_j - (m_i+m_j) B).
 // Bounded grid barrier of a cooperative launch (all blocks co-resident).  The
 // last block to arrive resets the count and bumps the generation; the others
 // wait on the generation with a sleep, and give up after `limit` polls,
@@ -603,26 +637,82 @@ __device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, co
     uint16_t* sl = s.sl;
     const T cc = a.c;
 
+    // The footprint's runs (same z-outer, y-inner order as the setup's
+    // footprint-local indices): lane r < 9 finds run r, then every lane gets
+    // all run starts and offsets by shuffles.
+    const FootRuns fr = foot_runs_warp(c, a.dim, a.nx, a.ny, a.nz, a.cell_start, lane);
+    const int Ftot = fr.total;
     int my_off = 0;
-    foot_runs(c, a.dim, a.nx, a.ny, a.nz, a.cell_start, [&](int ra, int rb, int off) {
-        for (int j = ra + lane; j < rb; j += 32) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) sv[d * F + off + (j - ra)] = __ldcg(a.v + (size_t)d * n + j);
-            sminv[off + (j - ra)] = T(1) / __ldg(a.mass + j);
-        }
-        if (cs >= ra && cs < rb) my_off = off + (cs - ra);
-    });
+    for (int r = 0; r < 9; ++r)
+        if (r < fr.nruns && cs >= fr.a[r] && cs < fr.a[r] + (fr.off[r + 1] - fr.off[r]))
+            my_off = fr.off[r] + (cs - fr.a[r]);
     const int np = ce - cs;
     const int p0 = __ldg(a.row_ptr + cs), p1 = __ldg(a.row_ptr + ce);
-    for (int k = p0 + lane; k < p1; k += 32) {
-        sw[k - p0] = __ldg(a.w + k);
-        sl[k - p0] = __ldg(a.loc + k);
+
+    // Staging in register batches: all loads of a batch are issued before
+    // any shared-memory store, so a batch costs one memory round trip.  v is
+    // read through L2 (ld.cg): other SMs wrote it in earlier colour phases.
+    constexpr int U = 8;
+    for (int base = 0; base < Ftot; base += 32 * U) {
+        T tv[U][D], tm[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = base + u * 32 + lane;
+            if (q < Ftot) {
+                const int j = fr.particle(q);
+#pragma unroll
+                for (int d = 0; d < D; ++d) tv[u][d] = __ldcg(a.v + (size_t)d * n + j);
+                tm[u] = __ldg(a.minv + j);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = base + u * 32 + lane;
+            if (q < Ftot) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) sv[d * F + q] = tv[u][d];
+                sminv[q] = tm[u];
+            }
+        }
     }
-    for (int p = lane; p <= np; p += 32) s.srow[p] = __ldg(a.row_ptr + cs + p) - p0;
-    for (int p = lane; p < np; p += 32) {
-        s.sm[p] = __ldg(a.mass + cs + p);
-        s.ssb[p] = cc * __ldg(a.sumw + cs + p);
-        s.ssb2[p] = cc * cc * __ldg(a.sumw2 + cs + p);
+    constexpr int U2 = 16;
+    for (int base = p0; base < p1; base += 32 * U2) {
+        T tw[U2];
+        uint16_t tl[U2];
+#pragma unroll
+        for (int u = 0; u < U2; ++u) {
+            const int k = base + u * 32 + lane;
+            if (k < p1) {
+                tw[u] = __ldg(a.w + k);
+                tl[u] = __ldg(a.loc + k);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U2; ++u) {
+            const int k = base + u * 32 + lane;
+            if (k < p1) {
+                sw[k - p0] = tw[u];
+                sl[k - p0] = tl[u];
+            }
+        }
+    }
+    for (int base = 0; base <= np; base += 32) {
+        const int p = base + lane;
+        int rp = 0;
+        T m = 0, s1 = 0, s2 = 0;
+        if (p <= np) rp = __ldg(a.row_ptr + cs + p) - p0;
+        if (p < np) {
+            m = __ldg(a.mass + cs + p);
+            s1 = __ldg(a.sumw + cs + p);
+            s2 = __ldg(a.sumw2 + cs + p);
+        }
+        if (p <= np) s.srow[p] = rp;
+        if (p < np) {
+            s.sm[p] = m;
+            s.ssb[p] = cc * s1;
+            s.ssb2[p] = cc * cc * s2;
+        }
     }
     __syncwarp();
 
@@ -696,12 +786,11 @@ __device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, co
         }
     }
     // write the footprint back (through L2: other SMs read it after the barrier)
-    foot_runs(c, a.dim, a.nx, a.ny, a.nz, a.cell_start, [&](int ra, int rb, int off) {
-        for (int j = ra + lane; j < rb; j += 32) {
+    for (int q = lane; q < Ftot; q += 32) {
+        const int j = fr.particle(q);
 #pragma unroll
-            for (int d = 0; d < D; ++d) __stcg(a.v + (size_t)d * n + j, sv[d * F + off + (j - ra)]);
-        }
-    });
+        for (int d = 0; d < D; ++d) __stcg(a.v + (size_t)d * n + j, sv[d * F + q]);
+    }
     __syncwarp();
 }
 
@@ -779,10 +868,13 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     s.ny = b->nc[1];
     s.nz = b->nc[2];
     s.cell_start = b->cell_start;
+    s.colour_cells = b->colour_cells;  // all colours; colour_ptr_d indexes into it
+    s.ncells_colour = b->ncells_nonempty;
     s.row_ptr = b->row_ptr;
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
     s.mass = static_cast<const T*>(b->mass);
+    s.minv = static_cast<const T*>(b->minv);
     s.sumw = static_cast<const T*>(b->sumw);
     s.sumw2 = static_cast<const T*>(b->sumw2);
     s.v = static_cast<T*>(b->v);
@@ -839,6 +931,11 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
     const int* cptr = b->colour_ptr_d;
     int ncol = b->ncolours;
     unsigned* bar = b->bar;
+    if (damping && (!sw.colour_cells || !sw.cell_start || !sw.row_ptr || !sw.loc || !sw.w ||
+                    !sw.mass || !sw.minv || !sw.sumw || !sw.sumw2 || !sw.v || !cptr || !bar)) {
+        set_error("damping sweep tables are not built");
+        return SRDR_ERR_INVALID;
+    }
     void* sweep_params[] = {&sw, &cptr, &ncol, &bar};
     cudaEvent_t ev = nullptr;
     auto counted = [&](int k, int nlaunch) {
