@@ -187,6 +187,34 @@ srdr_status srdr_body_kernel_times(const srdr_body* body, srdr_kernel_times* out
 void srdr_body_destroy(srdr_body* body);
 const char* srdr_last_error(void);
 
+/* Kinetic energy sum_i 1/2 m_i |v_i|^2 over the particles without
+ * SRDR_FLAG_CONSTRAINED, in FP64, computed WITHOUT ALLOCATING any device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc, such as codes whose device memory all belongs
+ * to their own pool or arena, or services that fix their device-memory
+ * footprint at start-up and refuse allocations afterwards.
+ *
+ * v: device array [3][n] (SoA: all x, then all y, then all z), mass: device
+ * [n], both FP64 when precision == SRDR_FP64 and FP32 when
+ * precision == SRDR_FP32_MIXED; flags: device [n] uint8 SRDR_FLAG_* bits or
+ * NULL (all free); ke_out: device pointer to one double.  All are owned by
+ * the caller.  The work is queued on cuda_stream and is complete when that
+ * stream is.
+ *
+ * The scratch space is a fixed array of 16384 FP64 partial sums (128 KiB)
+ * compiled into the library; every GPU that loads the library holds it until
+ * the process exits.  One partial covers 256 particles, so n may be at most
+ * 4,194,304; larger n returns SRDR_ERR_INVALID.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array: calls whose GPU work overlaps (different streams, or
+ * different host threads on one device) race and may return wrong sums, so
+ * order them on one stream.  Each call writes every partial it reads before
+ * reading it, so nothing is left over from an earlier call. */
+srdr_status srdr_kinetic_energy_noalloc(const void* v, const void* mass, const uint8_t* flags,
+                                        int64_t n, int precision, double* ke_out,
+                                        void* cuda_stream);
+
 /* The library's own Philox4x64-10 (host side of the device routine):
  * out[4] = Philox4x64-10(counter, key) and phi_n of the random choice. */
 void srdr_philox4x64_10(const uint64_t counter[4], const uint64_t key[2], uint64_t out[4]);

@@ -41,6 +41,7 @@ EXPORTS = [
     "srdr_body_info", "srdr_body_stats", "srdr_body_read_neighbours", "srdr_body_read_cells",
     "srdr_body_read_field", "srdr_body_destroy", "srdr_last_error", "srdr_philox4x64_10",
     "srdr_random_phi", "srdr_body_profile", "srdr_body_kernel_times",
+    "srdr_kinetic_energy_noalloc",
 ]
 KERNEL_CLASSES = ["pass_a", "pass_b", "sweep", "finish", "ke_final"]
 
