@@ -153,6 +153,7 @@ typedef struct {
     double eta, dt;        /* artificial viscosity and time step */
     int converged;         /* last relax met its criterion */
     int64_t launches;      /* kernels launched by step / relax calls since creation */
+    int sweep_cells_per_warp; /* damping-sweep mapping picked by the autotuner (1, 2, 4) */
 } srdr_stats;
 srdr_status srdr_body_stats(const srdr_body* body, srdr_stats* out);
 
@@ -182,9 +183,58 @@ typedef struct {
     int64_t intervals[SRDR_K_NCLASS];
 } srdr_kernel_times;
 srdr_status srdr_body_profile(srdr_body* body, int enable);
+
+/* Kernel mapping of the damping sweep: sweep_cells_per_warp = 1, 2 or 4 cells
+ * per warp, or 0 to let the autotuner time the three on the body's first
+ * damped step (the default).  The choice changes speed only: the sweep's sums
+ * follow one fixed order, so results are bitwise the same. */
+srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp);
 srdr_status srdr_body_kernel_times(const srdr_body* body, srdr_kernel_times* out);
 
 void srdr_body_destroy(srdr_body* body);
+
+/* Particles of the lattice body that srdr_body_create would build from desc. */
+srdr_status srdr_desc_particle_count(const srdr_body_desc* desc, int64_t* n_particles);
+
+/* ---------------------------------------------------------------- batches
+ * Many bodies of uneven sizes relaxed together.  Each body keeps its own
+ * device arrays; one batched step runs the stress pass, the force pass, the
+ * damping sweep (Sec. 3.1, on the bodies whose random choice damps this
+ * step, Sec. 3.3) colour-synchronised across the whole batch in one
+ * cooperative launch (Sec. 3.4), the displacement update and a per-body FP64
+ * kinetic-energy reduction, all bodies in shared launches captured as CUDA
+ * graphs.  A body's result is bitwise the same alone or in a batch.  The
+ * bodies must share dimension and precision; material, damping, alpha, seed,
+ * time step and size may differ. */
+typedef struct srdr_batch srdr_batch;
+
+/* Group existing bodies (caller-owned; they must outlive the batch).  The
+ * batch works on cuda_stream, or on a stream of its own if it is NULL. */
+srdr_status srdr_batch_create(srdr_body* const* bodies, int nbodies, void* cuda_stream,
+                              srdr_batch** out);
+/* nsteps batched steps of every body. */
+srdr_status srdr_batch_step(srdr_batch* batch, int64_t nsteps);
+/* Relax: every body retires at its own criterion KE < ke_ratio * KE_max
+ * (its work is then skipped and the work lists compacted); at most max_steps
+ * steps.  per_body_status[n] (SRDR_OK, SRDR_ERR_NOT_CONVERGED,
+ * SRDR_ERR_NONFINITE) and per_body_steps[n] may be NULL.  Returns the first
+ * non-OK per-body status, or SRDR_ERR_TIMEOUT if a grid barrier gave up. */
+srdr_status srdr_batch_run(srdr_batch* batch, double ke_ratio, int64_t max_steps,
+                           srdr_status* per_body_status, int64_t* per_body_steps);
+/* Steps run, kernels launched, and the autotuner's choices (damping-sweep
+ * cells per warp, threads per block of the passes); any may be NULL. */
+srdr_status srdr_batch_info(const srdr_batch* batch, int64_t* steps, int64_t* launches,
+                            int* sweep_cells_per_warp, int* pass_threads);
+/* Frees the batch (not the bodies it was created from). */
+void srdr_batch_destroy(srdr_batch* batch);
+
+/* One call: build lattice bodies from descs[nbodies], relax them as a batch,
+ * copy each displacement into host_disp_out[b] (caller-owned, 3 n_b doubles
+ * with n_b from srdr_desc_particle_count; NULL entries are skipped), free
+ * everything. */
+srdr_status srdr_batch_relax(const srdr_body_desc* descs, int nbodies, double ke_ratio,
+                             int64_t max_steps, double** host_disp_out,
+                             srdr_status* per_body_status);
 const char* srdr_last_error(void);
 
 /* Kinetic energy sum_i 1/2 m_i |v_i|^2 over the particles without

@@ -523,6 +523,23 @@ srdr_status srdr_body_stats(const srdr_body* b, srdr_stats* out)
     out->dt = b->dt;
     out->converged = b->converged;
     out->launches = b->launches;
+    out->sweep_cells_per_warp = b->sweep_cells_per_warp;
+    return SRDR_OK;
+}
+
+srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp)
+{
+    if (!b || (cells_per_warp != 0 && cells_per_warp != 1 && cells_per_warp != 2 &&
+               cells_per_warp != 4)) {
+        set_error("sweep_cells_per_warp must be 0 (autotune), 1, 2 or 4");
+        return SRDR_ERR_INVALID;
+    }
+    if (cells_per_warp == 0) {
+        b->sweep_tuned = 0;
+    } else {
+        b->sweep_tuned = 1;
+        b->sweep_cells_per_warp = cells_per_warp;
+    }
     return SRDR_OK;
 }
 

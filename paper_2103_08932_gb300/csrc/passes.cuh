@@ -1,0 +1,499 @@
+// ------------------------------------------------------------------ layouts
+// u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 hi/lo float4 [n] each.
+// PB (P B0): AoS, padded to whole 16-byte vectors: stride pb_stride<T, D>.
+template <typename T, int D>
+struct PBL;
+template <>
+struct PBL<float, 3> {
+    static constexpr int S = 12;
+    __device__ static void load(const float* p, int j, float (&m)[3][3])
+    {
+        const float4* q = reinterpret_cast<const float4*>(p + (size_t)j * S);
+        float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+        m[0][0] = a.x; m[0][1] = a.y; m[0][2] = a.z;
+        m[1][0] = a.w; m[1][1] = b.x; m[1][2] = b.y;
+        m[2][0] = b.z; m[2][1] = b.w; m[2][2] = c.x;
+    }
+    __device__ static void store(float* p, int j, const float (&m)[3][3])
+    {
+        float4* q = reinterpret_cast<float4*>(p + (size_t)j * S);
+        q[0] = make_float4(m[0][0], m[0][1], m[0][2], m[1][0]);
+        q[1] = make_float4(m[1][1], m[1][2], m[2][0], m[2][1]);
+        q[2] = make_float4(m[2][2], 0.f, 0.f, 0.f);
+    }
+};
+template <>
+struct PBL<float, 2> {
+    static constexpr int S = 4;
+    __device__ static void load(const float* p, int j, float (&m)[2][2])
+    {
+        float4 a = __ldg(reinterpret_cast<const float4*>(p + (size_t)j * S));
+        m[0][0] = a.x; m[0][1] = a.y; m[1][0] = a.z; m[1][1] = a.w;
+    }
+    __device__ static void store(float* p, int j, const float (&m)[2][2])
+    {
+        *reinterpret_cast<float4*>(p + (size_t)j * S) = make_float4(m[0][0], m[0][1], m[1][0], m[1][1]);
+    }
+};
+template <>
+struct PBL<double, 3> {
+    static constexpr int S = 10;
+    __device__ static void load(const double* p, int j, double (&m)[3][3])
+    {
+        const double2* q = reinterpret_cast<const double2*>(p + (size_t)j * S);
+        double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3), e = __ldg(q + 4);
+        m[0][0] = a.x; m[0][1] = a.y; m[0][2] = b.x;
+        m[1][0] = b.y; m[1][1] = c.x; m[1][2] = c.y;
+        m[2][0] = d.x; m[2][1] = d.y; m[2][2] = e.x;
+    }
+    __device__ static void store(double* p, int j, const double (&m)[3][3])
+    {
+        double2* q = reinterpret_cast<double2*>(p + (size_t)j * S);
+        q[0] = make_double2(m[0][0], m[0][1]);
+        q[1] = make_double2(m[0][2], m[1][0]);
+        q[2] = make_double2(m[1][1], m[1][2]);
+        q[3] = make_double2(m[2][0], m[2][1]);
+        q[4] = make_double2(m[2][2], 0.0);
+    }
+};
+template <>
+struct PBL<double, 2> {
+    static constexpr int S = 4;
+    __device__ static void load(const double* p, int j, double (&m)[2][2])
+    {
+        const double2* q = reinterpret_cast<const double2*>(p + (size_t)j * S);
+        double2 a = __ldg(q), b = __ldg(q + 1);
+        m[0][0] = a.x; m[0][1] = a.y; m[1][0] = b.x; m[1][1] = b.y;
+    }
+    __device__ static void store(double* p, int j, const double (&m)[2][2])
+    {
+        double2* q = reinterpret_cast<double2*>(p + (size_t)j * S);
+        q[0] = make_double2(m[0][0], m[0][1]);
+        q[1] = make_double2(m[1][0], m[1][1]);
+    }
+};
+
+// displacement access
+template <typename T>
+struct UAcc;
+template <>
+struct UAcc<double> {
+    // FP64: [n][4]
+    __device__ static void load(const double* u, const float*, const float*, int j, double (&x)[3],
+                                double (&)[3])
+    {
+        const double2* q = reinterpret_cast<const double2*>(u + (size_t)j * 4);
+        double2 a = __ldg(q), b = __ldg(q + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = b.x;
+    }
+    // u_i - u_j
+    __device__ static double diff(const double (&xi)[3], const double (&)[3], const double (&xj)[3],
+                                  const double (&)[3], int c)
+    {
+        return xi[c] - xj[c];
+    }
+};
+template <>
+struct UAcc<float> {
+    // FP32 mixed: u = hi + lo, two float4 arrays (about 48 significant bits)
+    __device__ static void load(const double*, const float* hi, const float* lo, int j, float (&h)[3],
+                                float (&l)[3])
+    {
+        float4 a = __ldg(reinterpret_cast<const float4*>(hi) + j);
+        float4 b = __ldg(reinterpret_cast<const float4*>(lo) + j);
+        h[0] = a.x; h[1] = a.y; h[2] = a.z;
+        l[0] = b.x; l[1] = b.y; l[2] = b.z;
+    }
+    // (hi_i - hi_j) + (lo_i - lo_j): the hi difference is exact when the two
+    // displacements are within a factor of two (Sterbenz), which is exactly
+    // the case where a plain FP32 difference would cancel
+    __device__ static float diff(const float (&hi)[3], const float (&li)[3], const float (&hj)[3],
+                                 const float (&lj)[3], int c)
+    {
+        return (hi[c] - hj[c]) + (li[c] - lj[c]);
+    }
+};
+
+// ------------------------------------------------------------------ stress
+// Given H = F - I, return P B0 with P = F S (Eq. piola), S from
+//   SVK (Eq. constitutive-equation): S = lambda tr(E) I + 2 mu E
+//   neo-Hookean (Eqs. strain-density, PK-stress): S = mu (I - C^-1) + lambda ln J C^-1
+// evaluated in forms free of cancellation at small strain:
+//   E = (H + H^T + H^T H) / 2, mu (I - C^-1) = 2 mu C^-1 E,
+//   J - 1 from the invariants of H, ln J = log1p(J - 1).
+template <typename T, int D, int MAT>
+__device__ inline void stress_PB(const T (&H)[D][D], const T (&B)[D][D], T lambda, T mu,
+                                 T (&PB)[D][D])
+{
+    T E[D][D];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            T s = H[p][q] + H[q][p];
+#pragma unroll
+            for (int r = 0; r < D; ++r) s += H[r][p] * H[r][q];
+            E[p][q] = T(0.5) * s;
+        }
+    T S[D][D];
+    if constexpr (MAT == SRDR_LINEAR_SVK) {
+        T tr = 0;
+#pragma unroll
+        for (int p = 0; p < D; ++p) tr += E[p][p];
+#pragma unroll
+        for (int p = 0; p < D; ++p)
+#pragma unroll
+            for (int q = 0; q < D; ++q) S[p][q] = T(2) * mu * E[p][q] + (p == q ? lambda * tr : T(0));
+    } else {
+        // J - 1 = det(I + H) - 1
+        T jm1;
+        if constexpr (D == 2) {
+            jm1 = H[0][0] + H[1][1] + (H[0][0] * H[1][1] - H[0][1] * H[1][0]);
+        } else {
+            T tr = H[0][0] + H[1][1] + H[2][2];
+            T tr2 = 0;
+#pragma unroll
+            for (int p = 0; p < D; ++p)
+#pragma unroll
+                for (int q = 0; q < D; ++q) tr2 += H[p][q] * H[q][p];
+            T det = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
+                    H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+                    H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+            jm1 = tr + T(0.5) * (tr * tr - tr2) + det;
+        }
+        T lnJ = log1p(jm1);
+        T J = T(1) + jm1;
+        T invdetC = T(1) / (J * J);  // det C = J^2
+        // C = I + 2E, C^-1 = adj(C) / det C
+        T C[D][D], Ci[D][D];
+#pragma unroll
+        for (int p = 0; p < D; ++p)
+#pragma unroll
+            for (int q = 0; q < D; ++q) C[p][q] = (p == q ? T(1) : T(0)) + T(2) * E[p][q];
+        if constexpr (D == 2) {
+            Ci[0][0] = C[1][1] * invdetC;
+            Ci[0][1] = -C[0][1] * invdetC;
+            Ci[1][0] = -C[1][0] * invdetC;
+            Ci[1][1] = C[0][0] * invdetC;
+        } else {
+            constexpr int P = 2;
+            Ci[0][0] = (C[1][1] * C[P][P] - C[1][P] * C[P][1]) * invdetC;
+            Ci[0][1] = (C[0][P] * C[P][1] - C[0][1] * C[P][P]) * invdetC;
+            Ci[0][P] = (C[0][1] * C[1][P] - C[0][P] * C[1][1]) * invdetC;
+            Ci[1][0] = (C[1][P] * C[P][0] - C[1][0] * C[P][P]) * invdetC;
+            Ci[1][1] = (C[0][0] * C[P][P] - C[0][P] * C[P][0]) * invdetC;
+            Ci[1][P] = (C[0][P] * C[1][0] - C[0][0] * C[1][P]) * invdetC;
+            Ci[P][0] = (C[1][0] * C[P][1] - C[1][1] * C[P][0]) * invdetC;
+            Ci[P][1] = (C[0][1] * C[P][0] - C[0][0] * C[P][1]) * invdetC;
+            Ci[P][P] = (C[0][0] * C[1][1] - C[0][1] * C[1][0]) * invdetC;
+        }
+#pragma unroll
+        for (int p = 0; p < D; ++p)
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                T ce = 0;
+#pragma unroll
+                for (int r = 0; r < D; ++r) ce += Ci[p][r] * E[r][q];
+                S[p][q] = T(2) * mu * ce + lambda * lnJ * Ci[p][q];
+            }
+    }
+    // P = F S = S + H S;  PB = P B0
+    T P[D][D];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            T s = S[p][q];
+#pragma unroll
+            for (int r = 0; r < D; ++r) s += H[p][r] * S[r][q];
+            P[p][q] = s;
+        }
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            T s = 0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) s += P[p][r] * B[r][q];
+            PB[p][q] = s;
+        }
+}
+
+// ------------------------------------------------------------------ pass A
+// H_i = -(sum_j u_ij (x) g_ij) B0_i with g_ij = V_j grad0_i W_ij, i.e. the
+// corrected displacement gradient at u^{n+1/2}; F = I + H.
+template <typename T, int D, int MAT>
+__device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
+{
+    const int n = a.n;
+    int s = i >> 5, lane = i & 31;
+    int base = __ldg(a.sell_ptr + s);
+    int width = (__ldg(a.sell_ptr + s + 1) - base) >> 5;
+    T xi[3], li[3];
+    UAcc<T>::load(a.u, a.uhi, a.ulo, i, xi, li);
+    T G[D][D];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) G[p][q] = 0;
+    // slots in batches of kUnroll: all stream loads, then all gathers, then
+    // the arithmetic, so each batch costs two memory round trips
+    for (int t0 = 0; t0 < width; t0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int k = base + (t0 + u) * 32 + lane;
+            const bool in = t0 + u < width;
+            jj[u] = in ? __ldg(a.sell_col + k) : i;
+            gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
+            gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
+            if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
+        }
+        T xj[kUnroll][3], lj[kUnroll][3];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) UAcc<T>::load(a.u, a.uhi, a.ulo, jj[u], xj[u], lj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int p = 0; p < D; ++p) {
+                T du = UAcc<T>::diff(xi, li, xj[u], lj[u], p);
+#pragma unroll
+                for (int q = 0; q < D; ++q) G[p][q] += du * gg[u][q];
+            }
+    }
+    T B[D][D], H[D][D], PB[D][D];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) B[p][q] = a.B0[(size_t)(p * D + q) * n + i];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            T s2 = 0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) s2 += G[p][r] * B[r][q];
+            H[p][q] = -s2;
+        }
+    stress_PB<T, D, MAT>(H, B, a.lambda, a.mu, PB);
+    PBL<T, D>::store(a.PB, i, PB);
+}
+
+template <typename T, int D, int MAT>
+__global__ void __launch_bounds__(kThreads) k_pass_a(StepArgs<T> a)
+{
+    if (a.sc->done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    pass_a_particle<T, D, MAT>(a, i);
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ inline double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Kinetic-energy partials: one per 32-particle slice, summed in a fixed
+// order by its warp (every lane of the warp must call this).  A body's KE is
+// then the same whether it is stepped alone or inside a batch.
+__device__ inline void slice_partial_store(double x, double* out, int i, int n)
+{
+    x = warp_sum(x);
+    const int slice = i >> 5;
+    if ((threadIdx.x & 31) == 0 && (slice << 5) < n) out[slice] = x;
+}
+
+// One block of kThreads: FP64 KE of one body from its slice partials in a
+// fixed order, its running maximum, the step counters and the relax test.
+__device__ inline void ke_finalize(const double* __restrict__ part, int np, DevScalars* sc,
+                                   int damped)
+{
+    __shared__ double s[kThreads / 32];
+    double x = 0.0;
+    for (int b = threadIdx.x; b < np; b += blockDim.x) x += part[b];
+    x = warp_sum(x);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) s[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ke = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) ke += s[k];
+        sc->ke = ke;
+        if (ke > sc->ke_max) sc->ke_max = ke;
+        sc->step += 1;
+        sc->damped += damped;
+        if (!isfinite(ke)) {
+            sc->status = DEV_NONFINITE;
+            sc->done = 1;
+        } else if (sc->tol > 0.0 && ke < sc->tol * sc->ke_max) {
+            sc->done = 1;
+        }
+    }
+}
+
+// u <- u + d, FP64 or FP32 hi/lo (two-sum with renormalisation)
+template <typename T>
+__device__ inline void u_add(const StepArgs<T>& a, int i, const T (&d)[3]);
+template <>
+__device__ inline void u_add<double>(const StepArgs<double>& a, int i, const double (&d)[3])
+{
+    double2* q = reinterpret_cast<double2*>(a.u + (size_t)i * 4);
+    double2 x = q[0], y = q[1];
+    x.x += d[0];
+    x.y += d[1];
+    y.x += d[2];
+    q[0] = x;
+    q[1] = y;
+}
+__device__ inline void two_sum_add(float& hi, float& lo, float d)
+{
+    float s = hi + d;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (d - bb);
+    float l2 = lo + e;
+    float h2 = s + l2;
+    lo = l2 - (h2 - s);
+    hi = h2;
+}
+template <>
+__device__ inline void u_add<float>(const StepArgs<float>& a, int i, const float (&d)[3])
+{
+    float4* ph = reinterpret_cast<float4*>(a.uhi) + i;
+    float4* pl = reinterpret_cast<float4*>(a.ulo) + i;
+    float4 h = *ph, l = *pl;
+    two_sum_add(h.x, l.x, d[0]);
+    two_sum_add(h.y, l.y, d[1]);
+    two_sum_add(h.z, l.z, d[2]);
+    *ph = h;
+    *pl = l;
+}
+
+// ------------------------------------------------------------------ pass B
+// dv_i/dt = (1/rho0) sum_j (PB_i + PB_j) g_ij + g, evaluated as
+// (1/rho0) [ sum_j (PB_j - PB_i) g_ij + 2 PB_i G_i ] + g with G_i = sum_j g_ij,
+// the same sum written without the cancellation of a nearly uniform stress.
+// Then v* = v^n + dt dv/dt (constrained: v = 0); on an undamped step also
+// u^{n+3/2} = u^{n+1/2} + dt v^{n+1} and the KE partials.
+template <typename T, int D>
+__device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_step)
+{
+    const int n = a.n;
+    double ke = 0.0;
+    {
+        int s = i >> 5, lane = i & 31;
+        int base = __ldg(a.sell_ptr + s);
+        int width = (__ldg(a.sell_ptr + s + 1) - base) >> 5;
+        T Pi[D][D];
+        PBL<T, D>::load(a.PB, i, Pi);
+        T acc[D];
+#pragma unroll
+        for (int p = 0; p < D; ++p) acc[p] = 0;
+        for (int t0 = 0; t0 < width; t0 += kUnroll) {
+            int jj[kUnroll];
+            T gg[kUnroll][D];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int k = base + (t0 + u) * 32 + lane;
+                const bool in = t0 + u < width;
+                jj[u] = in ? __ldg(a.sell_col + k) : i;
+                gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
+                gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
+                if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
+            }
+            T Pj[kUnroll][D][D];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, jj[u], Pj[u]);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int p = 0; p < D; ++p)
+#pragma unroll
+                    for (int q = 0; q < D; ++q) acc[p] += (Pj[u][p][q] - Pi[p][q]) * gg[u][q];
+        }
+        T Gi[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) Gi[q] = a.Gs[(size_t)q * n + i];
+#pragma unroll
+        for (int p = 0; p < D; ++p)
+#pragma unroll
+            for (int q = 0; q < D; ++q) acc[p] += T(2) * Pi[p][q] * Gi[q];
+        uint8_t f = a.flags[i];
+        T vi[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) vi[p] = a.v[(size_t)p * n + i];
+        if (f & SRDR_FLAG_CONSTRAINED) {
+            vi[0] = vi[1] = vi[2] = 0;
+        } else {
+#pragma unroll
+            for (int p = 0; p < D; ++p) {
+                T ap = acc[p] * a.inv_rho0 + a.grav[p];
+                if (f & SRDR_FLAG_END_LOAD) ap += a.endl[p];
+                vi[p] += a.dt * ap;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) a.v[(size_t)p * n + i] = vi[p];
+        if (final_step && !(f & SRDR_FLAG_CONSTRAINED)) {
+            T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
+            u_add<T>(a, i, d);
+            T m = a.mass[i];
+            ke = (double)(T(0.5) * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+        }
+    }
+    return ke;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_pass_b(StepArgs<T> a, int final_step)
+{
+    if (a.sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double ke = i < a.n ? pass_b_particle<T, D>(a, i, final_step) : 0.0;
+    if (final_step) slice_partial_store(ke, a.ke_part, i, a.n);
+}
+
+// after S_d: constraints, u^{n+3/2} = u^{n+1/2} + dt v^{n+1}, KE contribution
+template <typename T>
+__device__ inline double finish_particle(const StepArgs<T>& a, int i)
+{
+    const int n = a.n;
+    double ke = 0.0;
+    {
+        uint8_t f = a.flags[i];
+        if (f & SRDR_FLAG_CONSTRAINED) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) a.v[(size_t)p * n + i] = 0;
+        } else {
+            T vi[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) vi[p] = a.v[(size_t)p * n + i];
+            T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
+            u_add<T>(a, i, d);
+            T m = a.mass[i];
+            ke = (double)(T(0.5) * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+        }
+    }
+    return ke;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_finish(StepArgs<T> a)
+{
+    if (a.sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double ke = i < a.n ? finish_particle<T>(a, i) : 0.0;
+    slice_partial_store(ke, a.ke_part, i, a.n);
+}
+
+// one block: KE of the body, KE_max, step counters, relax test
+__global__ void __launch_bounds__(kThreads) k_ke_final(const double* __restrict__ part, int np,
+                                                        DevScalars* sc, int damped)
+{
+    if (sc->done) return;
+    ke_finalize(part, np, sc, damped);
+}
+

@@ -601,7 +601,8 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     b->nnz = nnz;
     T *w = nullptr, *sumw = nullptr, *sumw2 = nullptr, *Gs = nullptr, *B0 = nullptr, *PB = nullptr;
     SRDR_TRY(dalloc(b, &b->col, std::max(nnz, 1)));
-    SRDR_TRY(dalloc(b, &b->loc, std::max(nnz, 1)));
+    // 4 spare entries: the sweep copies loc as 32-bit words
+    SRDR_TRY(dalloc(b, &b->loc, (size_t)nnz + 4));
     SRDR_TRY(dalloc(b, &w, std::max(nnz, 1)));
     SRDR_TRY(dalloc(b, &sumw, n));
     SRDR_TRY(dalloc(b, &sumw2, n));
@@ -669,7 +670,7 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_TRY(dalloc(b, &v, (size_t)n * 3));
     b->v = v;
     SRDR_CK(cudaMemsetAsync(v, 0, sizeof(T) * (size_t)n * 3, st));
-    b->ke_blocks = nblocks(n);
+    b->ke_blocks = b->nslices;  // one FP64 partial per 32-particle slice
     SRDR_TRY(dalloc(b, &b->ke_part, b->ke_blocks));
     SRDR_CK(cudaMemsetAsync(b->ke_part, 0, sizeof(double) * b->ke_blocks, st));
 

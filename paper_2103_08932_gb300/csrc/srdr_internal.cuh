@@ -163,7 +163,8 @@ struct srdr_body {
     int max_foot = 0, max_pairs = 0, max_cell = 0;  // per-cell maxima
     int* colour_ptr_d = nullptr;     // device copy of colour_ptr
     unsigned* bar = nullptr;         // grid-barrier count and generation
-    int sweep_grid = 0;              // co-resident blocks of the sweep kernel
+    int sweep_cells_per_warp = 2;    // cells per warp of the sweep kernel (1, 2, 4)
+    int sweep_tuned = 0;
     int sweep_smem = 0;
 
     // host mirrors

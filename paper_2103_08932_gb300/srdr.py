@@ -41,7 +41,9 @@ EXPORTS = [
     "srdr_body_info", "srdr_body_stats", "srdr_body_read_neighbours", "srdr_body_read_cells",
     "srdr_body_read_field", "srdr_body_destroy", "srdr_last_error", "srdr_philox4x64_10",
     "srdr_random_phi", "srdr_body_profile", "srdr_body_kernel_times",
-    "srdr_kinetic_energy_noalloc",
+    "srdr_kinetic_energy_noalloc", "srdr_body_tune", "srdr_desc_particle_count",
+    "srdr_batch_create", "srdr_batch_step", "srdr_batch_run", "srdr_batch_info",
+    "srdr_batch_destroy", "srdr_batch_relax",
 ]
 KERNEL_CLASSES = ["pass_a", "pass_b", "sweep", "finish", "ke_final"]
 
@@ -78,7 +80,8 @@ class srdr_body_desc(C.Structure):
 class srdr_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("damped_steps", C.c_int64), ("ke", C.c_double),
                 ("ke_max", C.c_double), ("eta", C.c_double), ("dt", C.c_double),
-                ("converged", C.c_int), ("launches", C.c_int64)]
+                ("converged", C.c_int), ("launches", C.c_int64),
+                ("sweep_cells_per_warp", C.c_int)]
 
 
 class srdr_kernel_times(C.Structure):
@@ -120,6 +123,15 @@ def lib():
         "srdr_random_phi": (d, [C.c_uint64, C.c_uint64]),
         "srdr_body_profile": (st, [p, C.c_int]),
         "srdr_body_kernel_times": (st, [p, C.POINTER(srdr_kernel_times)]),
+        "srdr_body_tune": (st, [p, C.c_int]),
+        "srdr_desc_particle_count": (st, [C.POINTER(srdr_body_desc), C.POINTER(i64)]),
+        "srdr_batch_create": (st, [p, C.c_int, p, C.POINTER(p)]),
+        "srdr_batch_step": (st, [p, i64]),
+        "srdr_batch_run": (st, [p, d, i64, p, p]),
+        "srdr_batch_info": (st, [p, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)]),
+        "srdr_batch_destroy": (None, [p]),
+        "srdr_batch_relax": (st, [p, C.c_int, d, i64, p, p]),
     }
     for name, (rt, args) in sig.items():
         f = getattr(L, name)
@@ -249,6 +261,9 @@ class Body:
         _check(lib().srdr_body_stats(self.h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in srdr_stats._fields_}
 
+    def tune(self, sweep_cells_per_warp=0):
+        _check(lib().srdr_body_tune(self.h, int(sweep_cells_per_warp)))
+
     def profile(self, enable=True):
         _check(lib().srdr_body_profile(self.h, 1 if enable else 0))
 
@@ -287,3 +302,60 @@ def srdr_philox4x64_10(counter, key):
 
 def srdr_random_phi(seed, step):
     return lib().srdr_random_phi(seed, step)
+
+
+class Batch:
+    """Several bodies relaxed together (srdr_batch_*).  The bodies must
+    outlive the batch."""
+
+    def __init__(self, bodies, stream: int = 0):
+        self.bodies = list(bodies)
+        arr = (C.c_void_p * len(self.bodies))(*[b.h for b in self.bodies])
+        h = C.c_void_p()
+        _check(lib().srdr_batch_create(arr, len(self.bodies), C.c_void_p(stream), C.byref(h)))
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().srdr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps=1):
+        _check(lib().srdr_batch_step(self.h, int(nsteps)))
+
+    def run(self, ke_ratio=1e-8, max_steps=10**6):
+        nb = len(self.bodies)
+        st = np.zeros(nb, dtype=np.int32)
+        steps = np.zeros(nb, dtype=np.int64)
+        status = lib().srdr_batch_run(self.h, ke_ratio, int(max_steps), _ptr(st), _ptr(steps))
+        return status, st, steps
+
+    def info(self):
+        s, l, g, t = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+        _check(lib().srdr_batch_info(self.h, C.byref(s), C.byref(l), C.byref(g), C.byref(t)))
+        return {"steps": s.value, "launches": l.value, "sweep_cells_per_warp": g.value,
+                "pass_threads": t.value}
+
+
+def srdr_desc_particle_count(desc) -> int:
+    n = C.c_int64()
+    _check(lib().srdr_desc_particle_count(C.byref(desc), C.byref(n)))
+    return n.value
+
+
+def srdr_batch_relax(descs, ke_ratio=1e-8, max_steps=10**6):
+    """Build, relax and free a batch of lattice bodies; returns (status,
+    per-body status, list of displacement arrays [n_b][3])."""
+    nb = len(descs)
+    arr = (srdr_body_desc * nb)(*descs)
+    outs = [np.zeros((srdr_desc_particle_count(d), 3)) for d in descs]
+    ptrs = (C.c_void_p * nb)(*[o.ctypes.data for o in outs])
+    st = np.zeros(nb, dtype=np.int32)
+    status = lib().srdr_batch_relax(arr, nb, ke_ratio, int(max_steps), ptrs, _ptr(st))
+    return status, st, outs

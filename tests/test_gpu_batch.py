@@ -1,0 +1,104 @@
+"""Batched relaxation (one set of launches for many bodies of uneven sizes)
+against the same bodies relaxed one at a time through the C ABI.
+
+Every body keeps its own arithmetic and reduction order inside a batch, so
+the results must be BITWISE equal to the single-body runs, including the
+step at which each body meets its own kinetic-energy criterion."""
+import numpy as np
+import pytest
+
+from paper_2103_08932_gb300 import srdr
+from paper_2103_08932_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2103_08932_gb300 import build
+    build.build()
+    srdr.lib()
+
+
+def uneven_specs(dim=3):
+    if dim == 2:
+        return [
+            S.BodySpec(dim=2, extent=(0.04, 0.008, 0), dp=1e-3, clamp_axis=0, material=S.SVK,
+                       E=2e6, nu=0.3, gravity=(0, -9.81, 0), beta=0.5, L_char=0.008, alpha=0.2, seed=5),
+            S.BodySpec(dim=2, extent=(0.02, 0.006, 0), dp=1e-3, clamp_axis=0, material=S.NEO_HOOKEAN,
+                       E=1e6, nu=0.4, gravity=(0, -9.81, 0), beta=0.5, L_char=0.006, alpha=0.3, seed=6),
+        ]
+    return [
+        S.BodySpec(dim=3, extent=(0.02, 0.006, 0.006), dp=1e-3, clamp_axis=0, material=S.NEO_HOOKEAN,
+                   E=2e6, nu=0.3, gravity=(0, -9.81, 0), beta=0.5, L_char=0.006, alpha=0.2, seed=11),
+        S.BodySpec(dim=3, extent=(0.012, 0.008, 0.01), dp=1e-3, clamp_axis=0, material=S.SVK,
+                   E=5e5, nu=0.4, gravity=(0, 0, 0), end_load=(0, -30.0, 0), end_load_layer=True,
+                   beta=0.5, L_char=0.008, alpha=0.3, seed=12),
+        S.BodySpec(dim=3, extent=(0.008, 0.005, 0.005), dp=1e-3, clamp_axis=0, material=S.NEO_HOOKEAN,
+                   E=5e6, nu=0.25, gravity=(0, -9.81, 0), beta=0.5, L_char=0.005, alpha=0.5, seed=13),
+    ]
+
+
+@pytest.mark.parametrize("dim,precision", [(3, srdr.SRDR_FP64), (3, srdr.SRDR_FP32_MIXED),
+                                           (2, srdr.SRDR_FP64)])
+def test_batch_steps_equal_single_bodies(dim, precision):
+    specs = uneven_specs(dim)
+    single = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
+    for b in single:
+        b.step(40)
+    bodies = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
+    batch = srdr.Batch(bodies)
+    batch.step(40)
+    for a, b in zip(single, bodies):
+        assert np.array_equal(a.velocity(), b.velocity())
+        assert np.array_equal(a.displacement(), b.displacement())
+        sa, sb = a.stats(), b.stats()
+        assert sa["damped_steps"] == sb["damped_steps"] > 0
+        assert sa["ke"] == sb["ke"]
+    info = batch.info()
+    assert info["sweep_cells_per_warp"] in (1, 2, 4) and info["pass_threads"] in (128, 256, 512)
+    batch.close()
+
+
+def test_batch_relax_retires_each_body_at_its_own_step():
+    specs = uneven_specs(3)
+    tol = 1e-6
+    single_steps, single_u = [], []
+    for s in specs:
+        b = srdr.Body(srdr.make_desc(s))
+        status, steps, ratio = b.relax(tol, 200000)
+        single_steps.append(steps)
+        single_u.append(b.displacement())
+    bodies = [srdr.Body(srdr.make_desc(s)) for s in specs]
+    batch = srdr.Batch(bodies)
+    status, st, steps = batch.run(tol, 200000)
+    assert status == srdr.SRDR_OK and list(st) == [0] * len(specs)
+    assert list(steps) == single_steps
+    assert len(set(single_steps)) > 1  # the bodies really retire at different steps
+    for b, u in zip(bodies, single_u):
+        assert np.array_equal(b.displacement(), u)
+        assert b.stats()["converged"] == 1
+    batch.close()
+
+
+def test_batch_relax_one_call():
+    specs = uneven_specs(3)[:2]
+    descs = [srdr.make_desc(s) for s in specs]
+    status, st, outs = srdr.srdr_batch_relax(descs, 1e-6, 200000)
+    assert status == srdr.SRDR_OK and list(st) == [0, 0]
+    for s, u in zip(specs, outs):
+        b = srdr.Body(srdr.make_desc(s))
+        b.relax(1e-6, 200000)
+        assert np.array_equal(b.displacement(), u)
+
+
+def test_batch_step_cap_reports_not_converged():
+    specs = uneven_specs(3)[:1]
+    bodies = [srdr.Body(srdr.make_desc(s)) for s in specs]
+    batch = srdr.Batch(bodies)
+    status, st, steps = batch.run(1e-12, 50)
+    assert status == srdr.SRDR_ERR_NOT_CONVERGED
+    assert list(st) == [srdr.SRDR_ERR_NOT_CONVERGED] and list(steps) == [50]

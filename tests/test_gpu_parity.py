@@ -270,3 +270,21 @@ def test_undamped_and_zero_alpha():
     gb.step(5)
     assert ob.damped_steps == 0 and gb.stats()["damped_steps"] == 0
     assert rel(gb.velocity(), ob.v) < 1e-9
+
+
+# ------------------------------------------------------------------ sweep mapping
+@pytest.mark.parametrize("precision", [srdr.SRDR_FP64, srdr.SRDR_FP32_MIXED])
+def test_sweep_mapping_does_not_change_results(precision):
+    """1, 2 or 4 cells per warp (the autotuner's choices) give bitwise the
+    same velocities: the sweep's sums follow one 32-lane order."""
+    outs = []
+    for g in (1, 2, 4, 0):
+        b = gpu_for(SMALL3D, precision=precision)
+        b.tune(g)
+        b.step(12)
+        outs.append(b.velocity())
+        assert b.stats()["damped_steps"] > 0
+        if g == 0:
+            assert b.stats()["sweep_cells_per_warp"] in (1, 2, 4)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
