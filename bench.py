@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -42,7 +44,32 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["plate", "batched", "served", "block"], default="plate")
+    ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--served-max-n", type=float, default=2e4)
+    ap.add_argument("--served-tol", type=float, default=1e-8)
+    ap.add_argument("--served-max-steps", type=int, default=20000)
     return ap.parse_args()
+
+
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself when
+    torch.distributed is not initialised or has one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (replicas: each rank relaxes its own copy of the workload)."""
+    return world * units_per_rank * steps / (max_ms / 1e3)
 
 
 def dist_env():
@@ -231,12 +258,9 @@ def run_gpu(args):
     kt = body.kernel_times()
     st1 = body.stats()
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     n = body.n
-    value = world * n * args.steps / (ms / 1e3)
+    value = aggregate_rate(n, args.steps, world, ms)
     launches = int(st1["launches"] - st0["launches"])
     damped = int(st1["damped_steps"] - st0["damped_steps"])
 
@@ -307,10 +331,122 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batched(nbodies, n_lo, n_hi, steps, seed=3):
+    """Uneven bodies (counts log-uniform in [n_lo, n_hi], box / beam / plate,
+    aspect 1-20, E log-uniform 1e5-1e7, nu 0.2-0.45, gravity or end load):
+    `steps` steps of all of them as one batch vs the same steps one body at a
+    time, FP32-mixed, device time with CUDA events."""
+    import torch
+
+    from paper_2103_08932_gb300 import srdr
+    from paper_2103_08932_gb300 import synth as S
+    specs = S.random_bodies(nbodies, n_lo, n_hi, seed)
+    descs = [srdr.make_desc(s, precision=srdr.SRDR_FP32_MIXED) for s in specs]
+    bodies = [srdr.Body(d) for d in descs]
+    n_total = sum(b.n for b in bodies)
+    batch = srdr.Batch(bodies)
+    batch.step(8)  # warm-up, autotuner, graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(steps)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    info = batch.info()
+    batch.close()
+    t_alone = 0.0
+    for b in bodies:
+        b.step(8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(steps)
+        torch.cuda.synchronize()
+        t_alone += time.perf_counter() - t0
+        b.close()
+    return {"workload": f"{nbodies} bodies, particles log-uniform {int(n_lo)}-{int(n_hi)} "
+                        f"({n_total} in all), FP32-mixed, seed {seed}",
+            "steps": steps, "particles": n_total,
+            "batched_particle_steps_per_s": n_total * steps / t_batch,
+            "one_at_a_time_particle_steps_per_s": n_total * steps / t_alone,
+            "speedup": t_alone / t_batch, "launches_per_step": info["launches"] / max(1, info["steps"]),
+            "sweep_cells_per_warp": info["sweep_cells_per_warp"], "pass_threads": info["pass_threads"]}
+
+
+def run_served(rate, count, n_lo, n_hi, tol, max_steps, seed=4):
+    """Poisson request stream of uneven bodies into the continuous-batching
+    server: solves/s and p50/p99 submit-to-result latency."""
+    from paper_2103_08932_gb300 import srdr
+    from paper_2103_08932_gb300 import synth as S
+    specs = S.random_bodies(count, n_lo, n_hi, seed)
+    arrivals = S.poisson_arrivals(rate, count, seed)
+    srv = srdr.Server(64 << 30, ke_ratio=tol, max_steps=max_steps, max_bodies=256, chunk_steps=256)
+    t0 = time.perf_counter()
+    tickets = []
+    for s, ta in zip(specs, arrivals):
+        delay = t0 + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        st, t = srv.submit(srdr.make_desc(s, precision=srdr.SRDR_FP32_MIXED))
+        if st == srdr.SRDR_OK:
+            tickets.append(t)
+    statuses = [srv.wait(t, 3600.0)[0] for t in tickets]
+    rep = srv.stats()
+    srv.close()
+    return {"rate_per_s": rate, "requests": count,
+            "bodies": f"particles log-uniform {int(n_lo)}-{int(n_hi)}, KE/KE_max < {tol:g}, "
+                      f"cap {max_steps} steps, FP32-mixed, seed {seed}",
+            "solves_per_s": rep["solves_per_s"], "p50_latency_s": rep["p50_latency_s"],
+            "p99_latency_s": rep["p99_latency_s"], "peak_concurrent": rep["peak_concurrent"],
+            "converged": sum(1 for s in statuses if s == srdr.SRDR_OK),
+            "particle_steps_per_s": rep["particle_steps"] / max(1e-9, time.perf_counter() - t0)}
+
+
+def run_block(steps):
+    """The 0.1 m neo-Hookean cube at dp = 0.8 mm (125^3 body particles plus
+    3 fixed and 3 prescribed layers, 2.05 M particles), top face at -10 %:
+    FP32-mixed against an all-FP64 GPU run of the same steps."""
+    import torch
+
+    from paper_2103_08932_gb300 import srdr
+    from paper_2103_08932_gb300 import synth as S
+    spec = S.compression_block_3d()
+    out = {"workload": "compression block 0.1 m, dp = 0.8 mm, 125^3 + 6 layers, neo-Hookean "
+                       "E = 1e6, nu = 0.45, top -10 %, seed 2", "steps": steps}
+    us = {}
+    for name, prec in (("fp32_mixed", srdr.SRDR_FP32_MIXED), ("fp64", srdr.SRDR_FP64)):
+        b = srdr.Body(srdr.make_desc(spec, precision=prec))
+        b.step(3)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(steps - 3)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        us[name] = b.displacement()
+        out[name + "_particle_steps_per_s"] = b.n * (steps - 3) / (ms / 1e3)
+        out["particles"] = b.n
+        out["damped_steps"] = b.stats()["damped_steps"]
+        b.close()
+    d = us["fp32_mixed"] - us["fp64"]
+    moved = us["fp64"] - S.lattice(spec)[2]  # displacement from the initial field
+    out["max_rel_displacement_error_fp32_vs_fp64"] = float(np.abs(d).max() / np.abs(us["fp64"]).max())
+    out["max_rel_error_of_displacement_change"] = float(np.abs(d).max() / max(np.abs(moved).max(), 1e-300))
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        print(json.dumps({"impl": "gpu", "batched": run_batched(256, 1e3, 2e5, args.steps)}))
+    elif args.workload == "block":
+        print(json.dumps({"impl": "gpu", "block": run_block(args.steps)}))
+    elif args.workload == "served":
+        out = [run_served(r, args.requests, 1e3, args.served_max_n, args.served_tol,
+                          args.served_max_steps) for r in args.rates]
+        print(json.dumps({"impl": "gpu", "served": out}))
     else:
         run_gpu(args)
 

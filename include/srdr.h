@@ -185,10 +185,11 @@ typedef struct {
 srdr_status srdr_body_profile(srdr_body* body, int enable);
 
 /* Kernel mapping of the damping sweep: sweep_cells_per_warp = 1, 2 or 4 cells
- * per warp, or 0 to let the autotuner time the three on the body's first
- * damped step (the default).  The choice changes speed only: the sweep's sums
- * follow one fixed order, so results are bitwise the same. */
-srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp);
+ * per warp and sweep_warps_per_block = 1 or 4, or both 0 to let the
+ * autotuner time the six mappings on the body's first damped step (the
+ * default).  The choice changes speed only: the sweep's sums follow one fixed
+ * order, so results are bitwise the same. */
+srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp, int sweep_warps_per_block);
 srdr_status srdr_body_kernel_times(const srdr_body* body, srdr_kernel_times* out);
 
 void srdr_body_destroy(srdr_body* body);
@@ -227,6 +228,47 @@ srdr_status srdr_batch_info(const srdr_batch* batch, int64_t* steps, int64_t* la
                             int* sweep_cells_per_warp, int* pass_threads);
 /* Frees the batch (not the bodies it was created from). */
 void srdr_batch_destroy(srdr_batch* batch);
+
+/* ---------------------------------------------------------------- serving
+ * Relaxation requests served with continuous batching.  submit() queues a
+ * lattice body description (any host thread).  A worker thread admits queued
+ * requests while the number of live bodies is below max_bodies and their
+ * estimated device memory fits the budget, relaxes all live bodies together
+ * as one batch in chunks of steps, retires each body when its own KE falls
+ * below ke_ratio * KE_max (or after max_steps: SRDR_ERR_NOT_CONVERGED),
+ * copies its displacement to the host, frees its memory and admits the next
+ * requests.  Each result is bitwise the same as the same body relaxed alone
+ * (srdr_body_relax).  Internally synchronised. */
+typedef struct srdr_server srdr_server;
+typedef struct {
+    int64_t submitted, completed, refused, queued, in_flight;
+    int peak_concurrent;          /* most bodies live at once */
+    size_t bytes_in_use;          /* admitted device-memory estimate */
+    int64_t particle_steps;       /* over all finished chunks */
+    double p50_latency_s, p99_latency_s;  /* submit -> result, completed requests */
+    double solves_per_s;          /* completed / (last completion - first submit) */
+} srdr_server_report;
+
+/* device_mem_budget: bytes the live bodies may hold; cuda_stream as for bodies
+ * (NULL: the server makes its own).  Defaults: ke_ratio 1e-8, max_steps 1e6,
+ * max_bodies 256, chunks of 256 steps, queue of 4096. */
+srdr_status srdr_server_create(size_t device_mem_budget, void* cuda_stream, srdr_server** out);
+srdr_status srdr_server_configure(srdr_server* server, double ke_ratio, int64_t max_steps,
+                                  int max_bodies, int64_t chunk_steps, size_t queue_capacity);
+/* SRDR_ERR_BUSY if the queue is full, SRDR_ERR_NO_MEMORY if the request alone
+ * exceeds the budget. */
+srdr_status srdr_server_submit(srdr_server* server, const srdr_body_desc* desc, uint64_t* ticket);
+/* SRDR_ERR_BUSY while the request is unfinished; else its final status, with
+ * the displacement (3 n doubles, original order) in host_disp_out (may be
+ * NULL) and the submit-to-result latency.  A result is handed out once. */
+srdr_status srdr_server_poll(srdr_server* server, uint64_t ticket, double* host_disp_out, size_t n,
+                             double* latency_s);
+/* As poll, blocking up to timeout_s; steps (may be NULL) = steps taken. */
+srdr_status srdr_server_wait(srdr_server* server, uint64_t ticket, double timeout_s,
+                             double* host_disp_out, size_t n, double* latency_s, int64_t* steps);
+srdr_status srdr_server_stats(srdr_server* server, srdr_server_report* out);
+/* Stops the worker after its current chunk; unfinished requests are dropped. */
+void srdr_server_destroy(srdr_server* server);
 
 /* One call: build lattice bodies from descs[nbodies], relax them as a batch,
  * copy each displacement into host_disp_out[b] (caller-owned, 3 n_b doubles

@@ -527,18 +527,22 @@ srdr_status srdr_body_stats(const srdr_body* b, srdr_stats* out)
     return SRDR_OK;
 }
 
-srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp)
+srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp, int warps_per_block)
 {
-    if (!b || (cells_per_warp != 0 && cells_per_warp != 1 && cells_per_warp != 2 &&
-               cells_per_warp != 4)) {
-        set_error("sweep_cells_per_warp must be 0 (autotune), 1, 2 or 4");
+    const bool autotune = cells_per_warp == 0 && warps_per_block == 0;
+    const bool fixed = (cells_per_warp == 1 || cells_per_warp == 2 || cells_per_warp == 4) &&
+                       (warps_per_block == 1 || warps_per_block == 4);
+    if (!b || !(autotune || fixed)) {
+        set_error("sweep mapping must be (0, 0) for the autotuner, or cells per warp 1, 2, 4 "
+                  "and warps per block 1, 4");
         return SRDR_ERR_INVALID;
     }
-    if (cells_per_warp == 0) {
+    if (autotune) {
         b->sweep_tuned = 0;
     } else {
         b->sweep_tuned = 1;
         b->sweep_cells_per_warp = cells_per_warp;
+        b->sweep_warps_per_block = warps_per_block;
     }
     return SRDR_OK;
 }

@@ -164,6 +164,7 @@ struct srdr_body {
     int* colour_ptr_d = nullptr;     // device copy of colour_ptr
     unsigned* bar = nullptr;         // grid-barrier count and generation
     int sweep_cells_per_warp = 2;    // cells per warp of the sweep kernel (1, 2, 4)
+    int sweep_warps_per_block = 1;   // warps per block of the sweep kernel (1, 4)
     int sweep_tuned = 0;
     int sweep_smem = 0;
 

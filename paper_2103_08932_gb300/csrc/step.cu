@@ -109,30 +109,32 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     return s;
 }
 
-// The sweep kernel for G cells per warp, its shared memory and its grid
-// (co-resident blocks, at most one group per cell of the widest colour).
+// The sweep kernel for G cells per warp and W warps per block, its shared
+// memory and its grid (co-resident blocks, at most one group per cell of the
+// widest colour).
 template <typename T, int D>
 struct SweepLaunch {
     const void* fn = nullptr;
     size_t smem = 0;
     int grid = 0;
+    int threads = 32;
 };
 
-template <typename T, int D, int G>
-srdr_status sweep_launch_g(srdr_body* b, SweepLaunch<T, D>* out)
+template <typename T, int D, int G, int W>
+srdr_status sweep_launch_gw(srdr_body* b, SweepLaunch<T, D>* out)
 {
-    const size_t smem = (size_t)G * cell_smem_bytes<T, D>(b->max_foot, b->max_pairs, b->max_cell);
+    const size_t smem = (size_t)G * W * cell_smem_bytes<T, D>(b->max_foot, b->max_pairs, b->max_cell);
     if (smem > 227 * 1024) {
         set_error("damping sweep needs %zu bytes of shared memory per block (limit 227 KB)", smem);
         return SRDR_ERR_INVALID;
     }
-    const void* fn = (const void*)k_sweep_all<T, D, G>;
+    const void* fn = (const void*)k_sweep_all<T, D, G, W>;
     if (smem > 48 * 1024)
         SRDR_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, nsm = 0;
     SRDR_CK(cudaGetDevice(&dev));
     SRDR_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    SRDR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_all<T, D, G>, 32, smem));
+    SRDR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_all<T, D, G, W>, 32 * W, smem));
     if (per_sm < 1) {
         set_error("damping sweep kernel does not fit on an SM (%zu bytes of shared memory)", smem);
         return SRDR_ERR_INVALID;
@@ -142,24 +144,30 @@ srdr_status sweep_launch_g(srdr_body* b, SweepLaunch<T, D>* out)
         widest = std::max(widest, b->colour_ptr[c + 1] - b->colour_ptr[c]);
     out->fn = fn;
     out->smem = smem;
-    out->grid = std::max(1, std::min((widest + G - 1) / G, per_sm * nsm));
+    out->threads = 32 * W;
+    out->grid = std::max(1, std::min((widest + G * W - 1) / (G * W), per_sm * nsm));
     return SRDR_OK;
 }
 
 template <typename T, int D>
 srdr_status sweep_launch(srdr_body* b, SweepLaunch<T, D>* out)
 {
-    switch (b->sweep_cells_per_warp) {
-    case 1: return sweep_launch_g<T, D, 1>(b, out);
-    case 4: return sweep_launch_g<T, D, 4>(b, out);
-    default: return sweep_launch_g<T, D, 2>(b, out);
+    const int key = b->sweep_cells_per_warp * 10 + b->sweep_warps_per_block;
+    switch (key) {
+    case 11: return sweep_launch_gw<T, D, 1, 1>(b, out);
+    case 14: return sweep_launch_gw<T, D, 1, 4>(b, out);
+    case 21: return sweep_launch_gw<T, D, 2, 1>(b, out);
+    case 24: return sweep_launch_gw<T, D, 2, 4>(b, out);
+    case 41: return sweep_launch_gw<T, D, 4, 1>(b, out);
+    default: return sweep_launch_gw<T, D, 4, 4>(b, out);
     }
 }
 
-// Autotuner of the sweep's cells per warp: time G = 1, 2, 4 on a scratch
-// copy of v (the sweep writes v, the body's state must not change) and keep
-// the fastest.  The sweep's arithmetic does not depend on G (its reductions
-// follow one 32-lane order), so the choice changes speed, never results.
+// Autotuner of the sweep's mapping: time G = 1, 2, 4 cells per warp with
+// W = 1 or 4 warps per block on a scratch copy of v (the sweep writes v, the
+// body's state must not change) and keep the fastest.  The sweep's
+// arithmetic does not depend on the mapping (its reductions follow one
+// 32-lane order), so the choice changes speed, never results.
 template <typename T, int D>
 srdr_status autotune_sweep(srdr_body* b)
 {
@@ -178,26 +186,31 @@ srdr_status autotune_sweep(srdr_body* b)
     SRDR_CK(cudaEventCreate(&e0));
     SRDR_CK(cudaEventCreate(&e1));
     float best = 3.0e38f;
-    int best_g = b->sweep_cells_per_warp;
-    for (int g : {1, 2, 4}) {
-        b->sweep_cells_per_warp = g;
-        SweepLaunch<T, D> sl;
-        if (sweep_launch<T, D>(b, &sl) != SRDR_OK) continue;  // e.g. too much shared memory
-        SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(32), params, sl.smem, b->stream));
-        SRDR_CK(cudaEventRecord(e0, b->stream));
-        for (int r = 0; r < 2; ++r)
-            SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(32), params, sl.smem,
+    int best_g = b->sweep_cells_per_warp, best_w = b->sweep_warps_per_block;
+    for (int g : {1, 2, 4})
+        for (int w : {1, 4}) {
+            b->sweep_cells_per_warp = g;
+            b->sweep_warps_per_block = w;
+            SweepLaunch<T, D> sl;
+            if (sweep_launch<T, D>(b, &sl) != SRDR_OK) continue;  // e.g. too much shared memory
+            SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params, sl.smem,
                                                 b->stream));
-        SRDR_CK(cudaEventRecord(e1, b->stream));
-        SRDR_CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        SRDR_CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_g = g;
+            SRDR_CK(cudaEventRecord(e0, b->stream));
+            for (int r = 0; r < 2; ++r)
+                SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params,
+                                                    sl.smem, b->stream));
+            SRDR_CK(cudaEventRecord(e1, b->stream));
+            SRDR_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            SRDR_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_g = g;
+                best_w = w;
+            }
         }
-    }
     b->sweep_cells_per_warp = best_g;
+    b->sweep_warps_per_block = best_w;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return dev_free(b, vtmp);
@@ -244,7 +257,7 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         if (damp) {
             prof_begin(b, SRDR_K_SWEEP, &ev);
             const int nl = 1;
-            SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(grid), dim3(32),
+            SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(grid), dim3(sl.threads),
                                                 sweep_params, smem, st));
             prof_end(b, SRDR_K_SWEEP, ev);
             counted(SRDR_K_SWEEP, nl);

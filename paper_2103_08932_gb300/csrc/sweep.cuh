@@ -102,11 +102,13 @@ __device__ inline FootRuns foot_runs_group(int c, int dim, int nx, int ny, int n
 // last block to arrive resets the count and bumps the generation; the others
 // wait on the generation with a sleep, and give up after 2^24 polls, setting
 // DEV_TIMEOUT in sc->status so that the host gets an error instead of a hung
-// GPU.  One warp per block: lane 0 does the protocol.
+// GPU.  Thread 0 of the block does the protocol; every thread of the block
+// must call it.
 __device__ inline bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
                                     DevScalars* sc)
 {
-    __syncwarp();
+    __shared__ int s_ok;
+    __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
         unsigned g = *gen;
@@ -128,9 +130,10 @@ __device__ inline bool grid_barrier(unsigned* count, volatile unsigned* gen, uns
         }
         __threadfence();
         if (*(volatile int*)&sc->status == DEV_TIMEOUT) ok = 0;
+        s_ok = ok;
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    return ok != 0;
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // ---------------------------------------------------------------- shared memory
@@ -270,22 +273,50 @@ __device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, co
             // butterfly whatever L is: lane gl of the group keeps the 32/L
             // "virtual lanes" gl + w L (neighbours k = virtual lane mod 32)
             // and combines them as the first butterfly levels would, so the
-            // result does not depend on the cells-per-warp choice
+            // result does not depend on the cells-per-warp choice.  Rows of up
+            // to L*NK neighbours keep their indices, weights and velocities in
+            // registers: every shared-memory load of the particle is issued
+            // before any of its stores.
             constexpr int V = 32 / L;
+            constexpr int NK = L == 32 ? 4 : (L == 16 ? 8 : 12);
             T acc[V][D];
 #pragma unroll
             for (int w = 0; w < V; ++w)
 #pragma unroll
                 for (int d = 0; d < D; ++d) acc[w][d] = 0;
-            for (int kb = k0 + gl; kb < k1; kb += 32) {
+            const bool in_regs = k1 - k0 <= L * NK;
+            int jj[NK];
+            T BB[NK], vj[NK][D], im[NK];
+            if (in_regs) {
 #pragma unroll
-                for (int w = 0; w < V; ++w) {
-                    const int k = kb + w * L;
-                    if (k < k1) {
-                        const int j = sl[k];
-                        const T B = cc * sw[k];
+                for (int m = 0; m < NK; ++m) {
+                    const int k = k0 + gl + m * L;
+                    const bool ok = k < k1;
+                    jj[m] = ok ? (int)sl[k] : li;
+                    BB[m] = ok ? cc * sw[k] : T(0);
+                }
 #pragma unroll
-                        for (int d = 0; d < D; ++d) acc[w][d] -= B * (vi[d] - sv[d * F + j]);
+                for (int m = 0; m < NK; ++m) {
+#pragma unroll
+                    for (int d = 0; d < D; ++d) vj[m][d] = sv[d * F + jj[m]];
+                    im[m] = sminv[jj[m]];
+                }
+#pragma unroll
+                for (int m = 0; m < NK; ++m)
+                    if (k0 + gl + m * L < k1)
+#pragma unroll
+                        for (int d = 0; d < D; ++d) acc[m % V][d] -= BB[m] * (vi[d] - vj[m][d]);
+            } else {
+                for (int kb = k0 + gl; kb < k1; kb += 32) {
+#pragma unroll
+                    for (int w = 0; w < V; ++w) {
+                        const int k = kb + w * L;
+                        if (k < k1) {
+                            const int j = sl[k];
+                            const T B = cc * sw[k];
+#pragma unroll
+                            for (int d = 0; d < D; ++d) acc[w][d] -= B * (vi[d] - sv[d * F + j]);
+                        }
                     }
                 }
             }
@@ -310,14 +341,23 @@ __device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, co
                 vin[d] = vi[d] + sbm * kk[d];
             }
             // v_j <- v_j - B_j (v_i^new - v_j^p) / m_j,  v_j^p = v_j - B_j k
-            for (int k = k0 + gl; k < k1; k += L) {
-                const int j = sl[k];
-                const T B = cc * sw[k];
-                const T im = sminv[j];
+            if (in_regs) {
 #pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const T vj = sv[d * F + j];
-                    sv[d * F + j] = vj - B * (vin[d] - vj + B * kk[d]) * im;
+                for (int m = 0; m < NK; ++m)
+                    if (k0 + gl + m * L < k1)
+#pragma unroll
+                        for (int d = 0; d < D; ++d)
+                            sv[d * F + jj[m]] = vj[m][d] - BB[m] * (vin[d] - vj[m][d] + BB[m] * kk[d]) * im[m];
+            } else {
+                for (int k = k0 + gl; k < k1; k += L) {
+                    const int j = sl[k];
+                    const T B = cc * sw[k];
+                    const T imj = sminv[j];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        const T vjd = sv[d * F + j];
+                        sv[d * F + j] = vjd - B * (vin[d] - vjd + B * kk[d]) * imj;
+                    }
                 }
             }
             __syncwarp(gmask);
@@ -362,19 +402,23 @@ __device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, co
 
 // The whole S_d of one damped step in one cooperative launch: colours
 // 0..3^d-1 forward, then 3^d-1..0 backward, a bounded grid barrier between
-// colour phases; group g of block b takes cells b*G+g, +gridDim*G, ...
-template <typename T, int D, int G>
-__global__ void __launch_bounds__(32) k_sweep_all(SweepArgs<T> a, const int* __restrict__ colour_ptr,
-                                                  int ncolours, unsigned* bar)
+// colour phases.  Blocks of W warps, G cell groups per warp; group number
+// q = (block * W + warp) * G + g takes the colour's cells q, q + gridDim*W*G, ...
+// More warps per block means fewer blocks arriving at the grid barrier.
+template <typename T, int D, int G, int W>
+__global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int* __restrict__ colour_ptr,
+                                                      int ncolours, unsigned* bar)
 {
     constexpr int L = 32 / G;
     if (*(volatile int*)&a.sc->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = threadIdx.x / L, gl = threadIdx.x % L;
+    const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / L, gl = lane % L;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
     const size_t cell_bytes = cell_smem_bytes<T, D>(a.max_foot, a.max_pairs, a.max_cell);
-    const CellSmem<T, D> s =
-        cell_smem<T, D>(smem_raw + (size_t)g * cell_bytes, a.max_foot, a.max_pairs, a.max_cell);
+    const CellSmem<T, D> s = cell_smem<T, D>(smem_raw + (size_t)(wb * G + g) * cell_bytes, a.max_foot,
+                                             a.max_pairs, a.max_cell);
+    const int q0 = (blockIdx.x * W + wb) * G + g, qs = gridDim.x * W * G;
     int phases = 0;
     for (int ph = 0; ph < 2 * ncolours; ++ph) {
         const int backward = ph >= ncolours;
@@ -382,7 +426,7 @@ __global__ void __launch_bounds__(32) k_sweep_all(SweepArgs<T> a, const int* __r
         const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
         if (c1 == c0) continue;
         if (phases++ > 0 && !grid_barrier(bar, bar + 1, gridDim.x, a.sc)) return;
-        for (int cid = c0 + blockIdx.x * G + g; cid < c1; cid += gridDim.x * G)
+        for (int cid = c0 + q0; cid < c1; cid += qs)
             sweep_cell<T, D, L>(a, __ldg(a.colour_cells + cid), backward, s, gl, gmask);
         __syncwarp();
     }

@@ -43,7 +43,9 @@ EXPORTS = [
     "srdr_random_phi", "srdr_body_profile", "srdr_body_kernel_times",
     "srdr_kinetic_energy_noalloc", "srdr_body_tune", "srdr_desc_particle_count",
     "srdr_batch_create", "srdr_batch_step", "srdr_batch_run", "srdr_batch_info",
-    "srdr_batch_destroy", "srdr_batch_relax",
+    "srdr_batch_destroy", "srdr_batch_relax", "srdr_server_create", "srdr_server_configure",
+    "srdr_server_submit", "srdr_server_poll", "srdr_server_wait", "srdr_server_stats",
+    "srdr_server_destroy",
 ]
 KERNEL_CLASSES = ["pass_a", "pass_b", "sweep", "finish", "ke_final"]
 
@@ -123,7 +125,7 @@ def lib():
         "srdr_random_phi": (d, [C.c_uint64, C.c_uint64]),
         "srdr_body_profile": (st, [p, C.c_int]),
         "srdr_body_kernel_times": (st, [p, C.POINTER(srdr_kernel_times)]),
-        "srdr_body_tune": (st, [p, C.c_int]),
+        "srdr_body_tune": (st, [p, C.c_int, C.c_int]),
         "srdr_desc_particle_count": (st, [C.POINTER(srdr_body_desc), C.POINTER(i64)]),
         "srdr_batch_create": (st, [p, C.c_int, p, C.POINTER(p)]),
         "srdr_batch_step": (st, [p, i64]),
@@ -261,8 +263,8 @@ class Body:
         _check(lib().srdr_body_stats(self.h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in srdr_stats._fields_}
 
-    def tune(self, sweep_cells_per_warp=0):
-        _check(lib().srdr_body_tune(self.h, int(sweep_cells_per_warp)))
+    def tune(self, sweep_cells_per_warp=0, sweep_warps_per_block=0):
+        _check(lib().srdr_body_tune(self.h, int(sweep_cells_per_warp), int(sweep_warps_per_block)))
 
     def profile(self, enable=True):
         _check(lib().srdr_body_profile(self.h, 1 if enable else 0))
@@ -359,3 +361,80 @@ def srdr_batch_relax(descs, ke_ratio=1e-8, max_steps=10**6):
     st = np.zeros(nb, dtype=np.int32)
     status = lib().srdr_batch_relax(arr, nb, ke_ratio, int(max_steps), ptrs, _ptr(st))
     return status, st, outs
+
+
+class srdr_server_report(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("refused", C.c_int64),
+                ("queued", C.c_int64), ("in_flight", C.c_int64), ("peak_concurrent", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("particle_steps", C.c_int64),
+                ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
+                ("solves_per_s", C.c_double)]
+
+
+def _server_sigs(L):
+    p, i64, d = C.c_void_p, C.c_int64, C.c_double
+    for name, rt, args in [
+        ("srdr_server_create", C.c_int, [C.c_size_t, p, C.POINTER(p)]),
+        ("srdr_server_configure", C.c_int, [p, d, i64, C.c_int, i64, C.c_size_t]),
+        ("srdr_server_submit", C.c_int, [p, C.POINTER(srdr_body_desc), C.POINTER(C.c_uint64)]),
+        ("srdr_server_poll", C.c_int, [p, C.c_uint64, p, C.c_size_t, C.POINTER(d)]),
+        ("srdr_server_wait", C.c_int, [p, C.c_uint64, d, p, C.c_size_t, C.POINTER(d),
+                                       C.POINTER(i64)]),
+        ("srdr_server_stats", C.c_int, [p, C.POINTER(srdr_server_report)]),
+        ("srdr_server_destroy", None, [p]),
+    ]:
+        f = getattr(L, name)
+        f.restype = rt
+        f.argtypes = args
+
+
+class Server:
+    """Continuous-batching relaxation server (srdr_server_*)."""
+
+    def __init__(self, device_mem_budget, stream: int = 0, ke_ratio=1e-8, max_steps=10**6,
+                 max_bodies=256, chunk_steps=256, queue_capacity=4096):
+        L = lib()
+        _server_sigs(L)
+        h = C.c_void_p()
+        _check(L.srdr_server_create(int(device_mem_budget), C.c_void_p(stream), C.byref(h)))
+        self.h = h.value
+        _check(L.srdr_server_configure(self.h, ke_ratio, int(max_steps), int(max_bodies),
+                                       int(chunk_steps), int(queue_capacity)))
+        self.sizes = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().srdr_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, desc):
+        t = C.c_uint64()
+        st = lib().srdr_server_submit(self.h, C.byref(desc), C.byref(t))
+        if st != SRDR_OK:
+            return st, None
+        self.sizes[t.value] = srdr_desc_particle_count(desc)
+        return st, t.value
+
+    def poll(self, ticket):
+        out = np.zeros((self.sizes[ticket], 3))
+        lat = C.c_double()
+        st = lib().srdr_server_poll(self.h, ticket, _ptr(out), out.size, C.byref(lat))
+        return st, (out if st in (SRDR_OK, SRDR_ERR_NOT_CONVERGED) else None), lat.value
+
+    def wait(self, ticket, timeout_s=600.0):
+        out = np.zeros((self.sizes[ticket], 3))
+        lat, steps = C.c_double(), C.c_int64()
+        st = lib().srdr_server_wait(self.h, ticket, timeout_s, _ptr(out), out.size, C.byref(lat),
+                                    C.byref(steps))
+        return st, (out if st in (SRDR_OK, SRDR_ERR_NOT_CONVERGED) else None), lat.value, steps.value
+
+    def stats(self):
+        r = srdr_server_report()
+        _check(lib().srdr_server_stats(self.h, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in srdr_server_report._fields_}
