@@ -138,13 +138,15 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline bookkeeping
 def algorithmic_bytes(n, nnz, dim=3):
-    """Compulsory HBM bytes per launch of the FP32-mixed kernels: every array
-    the kernel must touch, once.  Neighbour gathers re-read arrays already
-    counted (they are meant to hit L2)."""
-    pairs = 16 * nnz  # sliced-ELL stream per pair: col int32 + V_j gradW (3 x fp32)
-    pass_a = pairs + n * (32 + 36 + 48)  # u hi/lo (2 x float4), B0 (9 f32), PB out (3 x float4)
-    pass_b = pairs + n * (48 + 12 + 24 + 64 + 1 + 4)  # PB, G, v r/w, u hi/lo r/w, flags, mass
-    return {"pass_a": pass_a, "pass_b": pass_b}
+    """Algorithmic HBM bytes per launch of the 3D FP32-mixed passes: a
+    neighbour stream of (col int32, s_ij fp32) = 8 B per pair, every
+    per-particle array the pass needs touched once, neighbour gathers counted
+    as L2 hits.  Pass A: u hi/lo read 24, B0 36, PB written 36, r0 12.
+    Pass B: PB 36, u hi/lo read and written 48, v read and written 24, r0 12,
+    mass 4, flags 1."""
+    pairs = 8 * nnz
+    return {"pass_a": pairs + n * (24 + 36 + 36 + 12),
+            "pass_b": pairs + n * (36 + 48 + 24 + 12 + 4 + 1)}
 
 
 def load_peaks():
@@ -268,7 +270,10 @@ def run_gpu(args):
     peak, peak_kind = load_peaks()
     ab = algorithmic_bytes(n, body.nnz)
     per = {k: (v["ms"] / max(v["intervals"], 1)) for k, v in kt.items()}
-    dom = max(("pass_a", "pass_b"), key=lambda k: kt[k]["ms"])
+    # the sweep: both directions of S_d in one launch, the CSR stream and the
+    # velocities read and written once per direction
+    ab["sweep"] = 2 * (8 * body.nnz + 28 * n)
+    dom = max(("pass_a", "pass_b", "sweep"), key=lambda k: kt[k]["ms"])
     achieved = ab[dom] / (per[dom] / 1e3) / 1e9
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")

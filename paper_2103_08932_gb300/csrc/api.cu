@@ -257,7 +257,7 @@ __global__ void k_read_uv(const int* __restrict__ perm, int n, const double* __r
     if (s >= n) return;
     int i = perm[s];
     for (int a = 0; a < 3; ++a) {
-        double vv = (double)v[(size_t)a * n + s];
+        double vv = (double)v[(size_t)s * 4 + a];
         double x;
         if (what == 0) {
             double uh = u ? u[(size_t)s * 4 + a] : (double)uhi[(size_t)s * 4 + a] + (double)ulo[(size_t)s * 4 + a];
@@ -278,8 +278,8 @@ __global__ void k_write_uv(const int* __restrict__ perm, int n, const double* __
     if (s >= n) return;
     int i = perm[s];
     for (int a = 0; a < 3; ++a) {
-        double vv = vin ? vin[(size_t)i * 3 + a] : (double)v[(size_t)a * n + s];
-        if (vin) v[(size_t)a * n + s] = (T)vv;
+        double vv = vin ? vin[(size_t)i * 3 + a] : (double)v[(size_t)s * 4 + a];
+        if (vin) v[(size_t)s * 4 + a] = (T)vv;
         if (uin) {
             double x = uin[(size_t)i * 3 + a] + half_dt * vv;  // u^{n+1/2}
             if (u) {

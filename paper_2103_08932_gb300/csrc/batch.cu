@@ -241,39 +241,6 @@ void bfree(srdr_batch* bt, void* p)
     cudaFree(p);
 }
 
-template <typename T>
-StepArgs<T> step_args(srdr_body* b)
-{
-    StepArgs<T> a{};
-    a.n = (int)b->n;
-    a.sell_ptr = b->sell_ptr;
-    a.sell_col = b->sell_col;
-    const T* sg = static_cast<const T*>(b->sell_g);
-    size_t ns = (size_t)std::max<int64_t>(b->nslots, 1);
-    a.g0 = sg;
-    a.g1 = sg + ns;
-    a.g2 = sg + 2 * ns;
-    a.B0 = static_cast<const T*>(b->B0);
-    a.PB = static_cast<T*>(b->PB);
-    a.Gs = static_cast<const T*>(b->Gs);
-    a.v = static_cast<T*>(b->v);
-    a.u = b->u;
-    a.uhi = b->uhi;
-    a.ulo = b->ulo;
-    a.flags = b->flags;
-    a.mass = static_cast<const T*>(b->mass);
-    a.ke_part = b->ke_part;
-    a.sc = b->sc;
-    a.lambda = (T)b->lambda;
-    a.mu = (T)b->mu;
-    a.inv_rho0 = (T)(1.0 / b->desc.rho0);
-    a.dt = (T)b->dt;
-    for (int p = 0; p < 3; ++p) {
-        a.grav[p] = (T)(p < b->dim ? b->desc.gravity[p] : 0.0);
-        a.endl[p] = (T)(p < b->dim ? b->desc.end_load[p] : 0.0);
-    }
-    return a;
-}
 
 template <typename T>
 SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
@@ -291,7 +258,6 @@ SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
     s.mass = static_cast<const T*>(b->mass);
-    s.minv = static_cast<const T*>(b->minv);
     s.sumw = static_cast<const T*>(b->sumw);
     s.sumw2 = static_cast<const T*>(b->sumw2);
     s.v = static_cast<T*>(b->v);
@@ -311,7 +277,7 @@ srdr_status upload_table(srdr_batch* bt)
     std::vector<BatchEntry<T>> tab(nb);
     for (int k = 0; k < nb; ++k) {
         srdr_body* b = bt->bodies[k];
-        tab[k].step = step_args<T>(b);
+        tab[k].step = make_step_args<T>(b);
         tab[k].sweep = sweep_args<T>(b, bt->F, bt->P, bt->C);
         tab[k].material = b->desc.material;
         tab[k].damping_on = b->desc.damping != SRDR_DAMP_NONE && b->desc.alpha > 0 && b->eta > 0;
@@ -550,9 +516,19 @@ srdr_status autotune(srdr_batch* bt)
     bt->G = best_g;
     best = 3.0e38f;
     int best_t = bt->pass_threads;
+    // the block size must fit the register use of both passes (FP64 3D uses
+    // more than 128 registers per thread, so 512 threads do not fit)
+    int limit = 1024;
+    for (const void* fn : {(const void*)k_batch_pass_a<T, D>, (const void*)k_batch_pass_b<T, D>}) {
+        cudaFuncAttributes fa;
+        SRDR_CK(cudaFuncGetAttributes(&fa, fn));
+        limit = std::min(limit, fa.maxThreadsPerBlock);
+    }
     for (int tpb : {128, 256, 512}) {
+        if (tpb > limit) continue;
         const int blocks = (int)(((int64_t)bt->nitems * 32 + tpb - 1) / tpb);
         float ms = 0;
+        // the stress pass only: it rewrites P B0 and leaves the state alone
         SRDR_TRY(timed([&] { k_batch_pass_a<T, D><<<blocks, tpb, 0, bt->stream>>>(tab, bt->items, bt->nitems); },
                        &ms));
         if (ms < best) {

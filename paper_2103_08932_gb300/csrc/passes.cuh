@@ -1,3 +1,5 @@
+#include "pairg.cuh"
+
 // ------------------------------------------------------------------ layouts
 // u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 hi/lo float4 [n] each.
 // PB (P B0): AoS, padded to whole 16-byte vectors: stride pb_stride<T, D>.
@@ -72,6 +74,20 @@ struct PBL<double, 2> {
         q[1] = make_double2(m[1][0], m[1][1]);
     }
 };
+
+// 1/2 m |v|^2 with explicit roundings: the same bits in every kernel that
+// evaluates it (no contraction choice left to the compiler)
+template <typename T>
+__device__ inline double ke_particle(T m, const T (&v)[3])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float s = __fmaf_rn(v[2], v[2], __fmaf_rn(v[1], v[1], __fmul_rn(v[0], v[0])));
+        return (double)__fmul_rn(__fmul_rn(0.5f, m), s);
+    } else {
+        const double s = __fma_rn(v[2], v[2], __fma_rn(v[1], v[1], __dmul_rn(v[0], v[0])));
+        return __dmul_rn(__dmul_rn(0.5, m), s);
+    }
+}
 
 // displacement access
 template <typename T>
@@ -237,7 +253,8 @@ __device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
 #pragma unroll
         for (int q = 0; q < D; ++q) G[p][q] = 0;
     // slots in batches of kUnroll: all stream loads, then all gathers, then
-    // the arithmetic, so each batch costs two memory round trips
+    // the arithmetic, so each batch costs two memory round trips.  Padding
+    // slots point at i itself with g = 0.
     for (int t0 = 0; t0 < width; t0 += kUnroll) {
         int jj[kUnroll];
         T gg[kUnroll][D];
@@ -314,7 +331,18 @@ __device__ inline void ke_finalize(const double* __restrict__ part, int np, DevS
 {
     __shared__ double s[kThreads / 32];
     double x = 0.0;
-    for (int b = threadIdx.x; b < np; b += blockDim.x) x += part[b];
+    // loads issued 16 at a time, added in index order (part[t], part[t + B], ...)
+    for (int b0 = threadIdx.x; b0 < np; b0 += 16 * blockDim.x) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int b = b0 + u * blockDim.x;
+            v[u] = b < np ? part[b] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+            if (b0 + u * (int)blockDim.x < np) x += v[u];
+    }
     x = warp_sum(x);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) s[w] = x;
@@ -422,9 +450,8 @@ __device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_
 #pragma unroll
             for (int q = 0; q < D; ++q) acc[p] += T(2) * Pi[p][q] * Gi[q];
         uint8_t f = a.flags[i];
-        T vi[3];
-#pragma unroll
-        for (int p = 0; p < 3; ++p) vi[p] = a.v[(size_t)p * n + i];
+        vec4_t<T> v4 = ld_v4<T>(a.v, i);
+        T vi[3] = {v4.x, v4.y, v4.z};
         if (f & SRDR_FLAG_CONSTRAINED) {
             vi[0] = vi[1] = vi[2] = 0;
         } else {
@@ -435,13 +462,14 @@ __device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_
                 vi[p] += a.dt * ap;
             }
         }
-#pragma unroll
-        for (int p = 0; p < 3; ++p) a.v[(size_t)p * n + i] = vi[p];
+        v4.x = vi[0];
+        v4.y = vi[1];
+        v4.z = vi[2];
+        st_v4<T>(a.v, i, v4);
         if (final_step && !(f & SRDR_FLAG_CONSTRAINED)) {
             T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
             u_add<T>(a, i, d);
-            T m = a.mass[i];
-            ke = (double)(T(0.5) * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+            ke = ke_particle<T>(a.mass[i], vi);
         }
     }
     return ke;
@@ -464,17 +492,15 @@ __device__ inline double finish_particle(const StepArgs<T>& a, int i)
     double ke = 0.0;
     {
         uint8_t f = a.flags[i];
+        vec4_t<T> v4 = ld_v4<T>(a.v, i);
         if (f & SRDR_FLAG_CONSTRAINED) {
-#pragma unroll
-            for (int p = 0; p < 3; ++p) a.v[(size_t)p * n + i] = 0;
+            v4.x = v4.y = v4.z = 0;
+            st_v4<T>(a.v, i, v4);
         } else {
-            T vi[3];
-#pragma unroll
-            for (int p = 0; p < 3; ++p) vi[p] = a.v[(size_t)p * n + i];
+            const T vi[3] = {v4.x, v4.y, v4.z};
             T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
             u_add<T>(a, i, d);
-            T m = a.mass[i];
-            ke = (double)(T(0.5) * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]));
+            ke = ke_particle<T>(a.mass[i], vi);
         }
     }
     return ke;
@@ -497,3 +523,41 @@ __global__ void __launch_bounds__(kThreads) k_ke_final(const double* __restrict_
     ke_finalize(part, np, sc, damped);
 }
 
+
+// ------------------------------------------------------------------ host: kernel arguments
+template <typename T>
+StepArgs<T> make_step_args(srdr_body* b)
+{
+    StepArgs<T> a{};
+    a.n = (int)b->n;
+    a.sell_ptr = b->sell_ptr;
+    a.sell_col = b->sell_col;
+    a.g0 = static_cast<const T*>(b->sell_g);
+    a.g1 = a.g0 + b->nslots;
+    a.g2 = a.g1 + b->nslots;
+    a.cpos = static_cast<const T*>(b->cpos);
+    a.ccell = b->ccell;
+    a.B0 = static_cast<const T*>(b->B0);
+    a.PB = static_cast<T*>(b->PB);
+    a.Gs = static_cast<const T*>(b->Gs);
+    a.v = static_cast<T*>(b->v);
+    a.u = b->u;
+    a.uhi = b->uhi;
+    a.ulo = b->ulo;
+    a.flags = b->flags;
+    a.mass = static_cast<const T*>(b->mass);
+    a.ke_part = b->ke_part;
+    a.sc = b->sc;
+    a.lambda = (T)b->lambda;
+    a.mu = (T)b->mu;
+    a.inv_rho0 = (T)(1.0 / b->desc.rho0);
+    a.dt = (T)b->dt;
+    a.rc = (T)b->rc;
+    a.inv_h = (T)(1.0 / b->h);
+    a.kc = (T)kernel_kc(b->dim, b->h);
+    for (int p = 0; p < 3; ++p) {
+        a.grav[p] = (T)(p < b->dim ? b->desc.gravity[p] : 0.0);
+        a.endl[p] = (T)(p < b->dim ? b->desc.end_load[p] : 0.0);
+    }
+    return a;
+}

@@ -19,6 +19,8 @@ constexpr int kThreads = 256;
 
 inline int nblocks(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
+#include "pairg.cuh"
+
 // Wendland C2 (h = support / 2): W(q) = a_d (1 - q/2)^4 (1 + 2q), q = r/h < 2, with
 // a_2 = 7 / (4 pi h^2), a_3 = 21 / (16 pi h^3).  Its radial derivative divided
 // by r is W'(r)/r = -5 a_d / h^2 (1 - q/2)^3, free of a division by r.
@@ -225,6 +227,59 @@ __global__ void k_gather(const int* __restrict__ perm, int n, const double* __re
     }
 }
 
+// per particle: offset inside its cell and volume, cpos = (r0 - lo - c r_c, V),
+// and the packed cell coordinates read by the pair kernel gradient
+template <typename T>
+__global__ void k_cell_pos(const double* __restrict__ r0, int n, Grid g, const int* __restrict__ cell_of,
+                           const T* __restrict__ mass, double rho0, T* __restrict__ cpos,
+                           int* __restrict__ ccell)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cell_of[i];
+    const int cc[3] = {c % g.nx, (c / g.nx) % g.ny, c / (g.nx * g.ny)};
+    const double lo[3] = {g.lo0, g.lo1, g.lo2};
+    for (int a = 0; a < 3; ++a) {
+        double o = 0.0;
+        if (a < g.dim) o = fma(-(double)cc[a], g.rc, r0[(size_t)a * n + i] - lo[a]);
+        cpos[(size_t)i * 4 + a] = (T)o;
+    }
+    cpos[(size_t)i * 4 + 3] = (T)((double)mass[i] / rho0);
+    ccell[i] = pack_cell(c, g.nx, g.ny);
+}
+
+// G_i = sum_j g_ij with the pair gradient the passes compute (FP64 sum), so
+// that sum_j (P_i + P_j) g_ij = sum_j (P_j - P_i) g_ij + 2 P_i G_i holds to
+// the rounding of the sums
+template <typename T, int D>
+__global__ void k_gsum(int n, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                       const T* __restrict__ cpos, const int* __restrict__ ccell, T rc, T inv_h,
+                       T kc, T* __restrict__ Gs)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const vec4_t<T> pi = load_cpos<T>(cpos, i);
+    const int ci = ccell[i];
+    double G[3] = {0, 0, 0};
+    for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        const int j = col[k];
+        T gg[D];
+        PairG<T>::template g<D>(pi, ci, load_cpos<T>(cpos, j), ccell[j], rc, inv_h, kc, gg);
+        for (int p = 0; p < D; ++p) G[p] += (double)gg[p];
+    }
+    for (int p = 0; p < 3; ++p) Gs[(size_t)p * n + i] = (T)G[p];
+}
+
+// velocity records (0, 0, 0, 1/m)
+template <typename T>
+__global__ void k_v_init(int n, const T* __restrict__ minv, T* __restrict__ v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = 0; a < 3; ++a) v[(size_t)i * 4 + a] = T(0);
+    v[(size_t)i * 4 + 3] = minv[i];
+}
+
 // colour = sum_a (i_a mod 3) 3^a, per non-empty cell
 __device__ inline int cell_colour(int c, int dim, int nx, int ny)
 {
@@ -295,15 +350,15 @@ __global__ void k_csr_count(const double* __restrict__ r0, int n, int dim, int n
 }
 
 // neighbours (ascending original id), footprint-local index, damping weight
-// w_ij = V_i V_j W'(r)/r, and per particle: sum w, sum w^2, G_i = sum_j V_j
-// grad0_i W_ij, and B0_i = (-sum_j V_j r0_ij (x) grad0_i W_ij)^-1 (in FP64).
+// w_ij = V_i V_j W'(r)/r, and per particle: sum w, sum w^2 and
+// B0_i = (-sum_j V_j r0_ij (x) grad0_i W_ij)^-1 (in FP64).
 template <typename T>
 __global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx, int ny, int nz,
                            const int* __restrict__ start, const int* __restrict__ cell_of,
                            double rc2, double h, double rho0, const T* __restrict__ mass,
                            const int* __restrict__ row_ptr, int* __restrict__ col,
                            uint16_t* __restrict__ loc, T* __restrict__ w, T* __restrict__ sumw,
-                           T* __restrict__ sumw2, T* __restrict__ Gs, T* __restrict__ B0,
+                           T* __restrict__ sumw2, T* __restrict__ B0,
                            const int* __restrict__ perm, DevScalars* sc)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -311,7 +366,6 @@ __global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx
     int k = row_ptr[i];
     double Vi = (double)mass[i] / rho0;
     double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    double G[3] = {0, 0, 0};
     double sw = 0.0, sw2 = 0.0;
     for_footprint(cell_of[i], dim, nx, ny, nz, start, [&](int a, int b, int off) {
         for (int j = a; j < b; ++j) {
@@ -323,10 +377,8 @@ __global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx
             double Vj = (double)mass[j] / rho0;
             double x[3] = {0, 0, 0};
             for (int q = 0; q < dim; ++q) x[q] = r0[(size_t)q * n + i] - r0[(size_t)q * n + j];
-            for (int p = 0; p < dim; ++p) {
-                G[p] += Vj * f * x[p];
+            for (int p = 0; p < dim; ++p)
                 for (int q = 0; q < dim; ++q) M[p][q] -= Vj * f * x[p] * x[q];
-            }
             double wij = Vi * Vj * f;
             sw += wij;
             sw2 += wij * wij;
@@ -360,7 +412,6 @@ __global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx
     }
     sumw[i] = (T)sw;
     sumw2[i] = (T)sw2;
-    for (int p = 0; p < 3; ++p) Gs[(size_t)p * n + i] = (T)G[p];
     double inv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     double det;
     if (dim == 2) {
@@ -404,10 +455,13 @@ __global__ void k_sell_width(const int* __restrict__ row_ptr, int n, int nslices
     slots[s] = wmax * 32;
 }
 
-template <typename T>
-__global__ void k_sell_fill(const double* __restrict__ r0, int n, int dim, double h, double rho0,
-                            const T* __restrict__ mass, const int* __restrict__ row_ptr,
-                            const int* __restrict__ col, const int* __restrict__ sell_ptr,
+// sliced ELL: slot (slice s, column t, lane l) holds neighbour t of particle
+// 32 s + l and g_ij from the same formula that gives G_i; padding slots hold
+// the particle itself with g = 0
+template <typename T, int D>
+__global__ void k_sell_fill(int n, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                            const int* __restrict__ sell_ptr, const T* __restrict__ cpos,
+                            const int* __restrict__ ccell, T rc, T inv_h, T kc,
                             int* __restrict__ scol, T* __restrict__ sg, int64_t nslots)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -415,22 +469,20 @@ __global__ void k_sell_fill(const double* __restrict__ r0, int n, int dim, doubl
     int s = i >> 5, lane = i & 31;
     int base = sell_ptr[s], width = (sell_ptr[s + 1] - base) >> 5;
     int k0 = row_ptr[i], deg = row_ptr[i + 1] - k0;
+    const vec4_t<T> pi = load_cpos<T>(cpos, i);
+    const int ci = ccell[i];
     for (int t = 0; t < width; ++t) {
         int64_t slot = (int64_t)base + t * 32 + lane;
-        double g[3] = {0, 0, 0};
-        int j = i;  // padding: self with zero weight contributes nothing
+        T g[3] = {0, 0, 0};
+        int j = i;
         if (t < deg) {
             j = col[k0 + t];
-            double x[3] = {0, 0, 0}, d2 = 0;
-            for (int q = 0; q < dim; ++q) {
-                x[q] = r0[(size_t)q * n + i] - r0[(size_t)q * n + j];
-                d2 += x[q] * x[q];
-            }
-            double f = wendland_dw_over_r(dim, h, sqrt(d2)) * (double)mass[j] / rho0;
-            for (int q = 0; q < dim; ++q) g[q] = f * x[q];
+            T gg[D];
+            PairG<T>::template g<D>(pi, ci, load_cpos<T>(cpos, j), ccell[j], rc, inv_h, kc, gg);
+            for (int q = 0; q < D; ++q) g[q] = gg[q];
         }
         scol[slot] = j;
-        for (int q = 0; q < 3; ++q) sg[(size_t)q * nslots + slot] = (T)g[q];
+        for (int q = 0; q < 3; ++q) sg[(size_t)q * nslots + slot] = g[q];
     }
 }
 
@@ -619,8 +671,25 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_CK(cudaMemsetAsync(PB, 0, sizeof(T) * (size_t)n * b->pb_stride, st));
     k_csr_fill<T><<<nblocks(n), kThreads, 0, st>>>(b->r0, n, dim, g.nx, g.ny, g.nz, b->cell_start,
                                                    b->cell_of, rc2, b->h, b->desc.rho0, mass,
-                                                   b->row_ptr, b->col, b->loc, w, sumw, sumw2, Gs,
-                                                   B0, b->perm, b->sc);
+                                                   b->row_ptr, b->col, b->loc, w, sumw, sumw2, B0,
+                                                   b->perm, b->sc);
+    SRDR_CK(cudaGetLastError());
+
+    // per-particle cell offsets and packed cells, then G_i from the same pair
+    // gradient the passes evaluate
+    T* cpos = nullptr;
+    SRDR_TRY(dalloc(b, &cpos, (size_t)n * 4));
+    SRDR_TRY(dalloc(b, &b->ccell, n));
+    b->cpos = cpos;
+    k_cell_pos<T><<<nblocks(n), kThreads, 0, st>>>(b->r0, n, g, b->cell_of, mass, b->desc.rho0, cpos,
+                                                   b->ccell);
+    const T rcT = (T)b->rc, ihT = (T)(1.0 / b->h), kcT = (T)kernel_kc(dim, b->h);
+    if (dim == 2)
+        k_gsum<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, cpos, b->ccell, rcT, ihT,
+                                                      kcT, Gs);
+    else
+        k_gsum<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, cpos, b->ccell, rcT, ihT,
+                                                      kcT, Gs);
     SRDR_CK(cudaGetLastError());
 
     // sliced ELL for the passes
@@ -639,12 +708,16 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     }
     b->nslots = nslots;
     T* sg = nullptr;
-    SRDR_TRY(dalloc(b, &b->sell_col, std::max(nslots, 1)));
-    SRDR_TRY(dalloc(b, &sg, (size_t)std::max(nslots, 1) * 3));
+    const int64_t ns = std::max(nslots, 1);
+    SRDR_TRY(dalloc(b, &b->sell_col, ns));
+    SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
     b->sell_g = sg;
-    k_sell_fill<T><<<nblocks(n), kThreads, 0, st>>>(b->r0, n, dim, b->h, b->desc.rho0, mass,
-                                                    b->row_ptr, b->col, b->sell_ptr, b->sell_col,
-                                                    sg, std::max(nslots, 1));
+    if (dim == 2)
+        k_sell_fill<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
+                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
+    else
+        k_sell_fill<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
+                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
 
     // footprint maxima size the damping sweep's shared memory
     int* fs = nullptr;
@@ -667,9 +740,9 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     }
     // velocity state and KE partials
     T* v = nullptr;
-    SRDR_TRY(dalloc(b, &v, (size_t)n * 3));
+    SRDR_TRY(dalloc(b, &v, (size_t)n * 4));
     b->v = v;
-    SRDR_CK(cudaMemsetAsync(v, 0, sizeof(T) * (size_t)n * 3, st));
+    k_v_init<T><<<nblocks(n), kThreads, 0, st>>>(n, minv, v);
     b->ke_blocks = b->nslices;  // one FP64 partial per 32-particle slice
     SRDR_TRY(dalloc(b, &b->ke_part, b->ke_blocks));
     SRDR_CK(cudaMemsetAsync(b->ke_part, 0, sizeof(double) * b->ke_blocks, st));

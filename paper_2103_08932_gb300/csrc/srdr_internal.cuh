@@ -8,7 +8,8 @@
 //   u     FP64 [n][4] (FP64 mode) or FP32 hi and lo arrays [n][4] (FP32 mode,
 //         u = hi + lo), held at the half step u^{n+1/2}; AoS so that one
 //         neighbour gather is one or two 16-byte loads
-//   v     T [3][n]
+//   v     T [n][4] velocity records (vx, vy, vz, 1/m): one 16-byte (FP32) or
+//         two 16-byte (FP64) accesses per particle
 //   B0    T [D*D][n] row-major tensor components, SoA (read by the owner only)
 //   PB    T [n][pb_stride] AoS padded to 16-byte vectors (gathered)
 //   G     T [3][n]   sum_j V_j grad W_ij (for the difference form of the force)
@@ -16,7 +17,10 @@
 //         loc uint16 [nnz] (index of j inside the 3^d-cell footprint of
 //         cell(i)), w T [nnz] = V_i V_j W'(r)/r  (damping sweep)
 //   SELL  32-row slices: sell_ptr int32 [nslices+1], sell_col int32 [slots],
-//         sell_g T [3][slots] = V_j grad0_i W_ij  (stress and force passes)
+//         sell_g T [3][slots] = g_ij = V_j grad0_i W_ij (stress and force passes)
+//   cpos  T [n][4] offset inside its cell and volume V; ccell int32 [n]
+//         packed cell coordinates: g_ij and G_i = sum_j g_ij are evaluated
+//         from them by one rounding-exact formula (pairg.cuh)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -67,13 +71,15 @@ struct StepArgs {
     int n;
     const int* __restrict__ sell_ptr;
     const int* __restrict__ sell_col;
-    const T* __restrict__ g0;
-    const T* __restrict__ g1;
-    const T* __restrict__ g2;
+    const T* __restrict__ g0;   // [slots] V_j grad0_i W_ij, x component (sliced ELL)
+    const T* __restrict__ g1;   // y component
+    const T* __restrict__ g2;   // z component
+    const T* __restrict__ cpos;   // [n][4] offset in its cell (x, y, z) and volume
+    const int* __restrict__ ccell; // [n] packed cell coordinates x | y << 10 | z << 20
     const T* __restrict__ B0;   // [D*D][n]
-    T* __restrict__ PB;         // [D*D][n]
+    T* __restrict__ PB;         // [n][pb_stride]
     const T* __restrict__ Gs;   // [3][n]
-    T* __restrict__ v;          // [3][n]
+    T* __restrict__ v;          // [n][4] (vx, vy, vz, 1/m)
     double* __restrict__ u;     // [3][n] FP64 mode
     float* __restrict__ uhi;    // [3][n] FP32 mode
     float* __restrict__ ulo;    // [3][n] FP32 mode
@@ -82,6 +88,7 @@ struct StepArgs {
     double* __restrict__ ke_part;
     DevScalars* sc;
     T lambda, mu, inv_rho0, dt;
+    T rc, inv_h, kc;             // cell edge, 1/h, -5 alpha_d / h^2
     T grav[3];
     T endl[3];
 };
@@ -98,7 +105,6 @@ struct SweepArgs {
     const uint16_t* __restrict__ loc;
     const T* __restrict__ w;
     const T* __restrict__ mass;
-    const T* __restrict__ minv;
     const T* __restrict__ sumw;
     const T* __restrict__ sumw2;
     T* __restrict__ v;
@@ -144,7 +150,9 @@ struct srdr_body {
     int64_t nslots = 0;
     int* sell_ptr = nullptr;
     int* sell_col = nullptr;
-    void* sell_g = nullptr;     // T [3][nslots]
+    void* sell_g = nullptr;     // T [3][slots] pair gradients in sliced-ELL order
+    void* cpos = nullptr;       // T [n][4] offset in its cell and volume
+    int* ccell = nullptr;       // [n] packed cell coordinates
     void* B0 = nullptr;         // T [D*D][n]
     void* PB = nullptr;
     void* Gs = nullptr;         // T [3][n]
@@ -191,6 +199,15 @@ template <typename P>
 inline srdr_status dalloc(srdr_body* b, P** p, size_t count)
 {
     return dev_alloc(b, reinterpret_cast<void**>(p), count * sizeof(P));
+}
+
+// -5 alpha_d / h^2 of the Wendland C2 kernel: W'(r)/r = kc (1 - r/(2h))^3,
+// alpha_2 = 7 / (4 pi h^2), alpha_3 = 21 / (16 pi h^3)
+inline double kernel_kc(int dim, double h)
+{
+    const double pi = 3.14159265358979323846;
+    const double a = dim == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
+    return -5.0 * a / (h * h);
 }
 
 // elements per particle of the AoS P B0 array (whole 16-byte vectors)

@@ -45,39 +45,6 @@ __global__ void k_set_tol(DevScalars* sc, double tol)
 }
 
 // ------------------------------------------------------------------ host side
-template <typename T>
-StepArgs<T> make_step_args(srdr_body* b)
-{
-    StepArgs<T> a{};
-    a.n = (int)b->n;
-    a.sell_ptr = b->sell_ptr;
-    a.sell_col = b->sell_col;
-    const T* sg = static_cast<const T*>(b->sell_g);
-    size_t ns = (size_t)std::max<int64_t>(b->nslots, 1);
-    a.g0 = sg;
-    a.g1 = sg + ns;
-    a.g2 = sg + 2 * ns;
-    a.B0 = static_cast<const T*>(b->B0);
-    a.PB = static_cast<T*>(b->PB);
-    a.Gs = static_cast<const T*>(b->Gs);
-    a.v = static_cast<T*>(b->v);
-    a.u = b->u;
-    a.uhi = b->uhi;
-    a.ulo = b->ulo;
-    a.flags = b->flags;
-    a.mass = static_cast<const T*>(b->mass);
-    a.ke_part = b->ke_part;
-    a.sc = b->sc;
-    a.lambda = (T)b->lambda;
-    a.mu = (T)b->mu;
-    a.inv_rho0 = (T)(1.0 / b->desc.rho0);
-    a.dt = (T)b->dt;
-    for (int p = 0; p < 3; ++p) {
-        a.grav[p] = (T)(p < b->dim ? b->desc.gravity[p] : 0.0);
-        a.endl[p] = (T)(p < b->dim ? b->desc.end_load[p] : 0.0);
-    }
-    return a;
-}
 
 template <typename T>
 SweepArgs<T> make_sweep_args(srdr_body* b)
@@ -95,7 +62,6 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
     s.mass = static_cast<const T*>(b->mass);
-    s.minv = static_cast<const T*>(b->minv);
     s.sumw = static_cast<const T*>(b->sumw);
     s.sumw2 = static_cast<const T*>(b->sumw2);
     s.v = static_cast<T*>(b->v);
@@ -173,8 +139,8 @@ srdr_status autotune_sweep(srdr_body* b)
 {
     b->sweep_tuned = 1;
     T* vtmp = nullptr;
-    SRDR_TRY(dalloc(b, &vtmp, (size_t)3 * b->n));
-    SRDR_CK(cudaMemcpyAsync(vtmp, b->v, sizeof(T) * 3 * (size_t)b->n, cudaMemcpyDeviceToDevice,
+    SRDR_TRY(dalloc(b, &vtmp, (size_t)4 * b->n));
+    SRDR_CK(cudaMemcpyAsync(vtmp, b->v, sizeof(T) * 4 * (size_t)b->n, cudaMemcpyDeviceToDevice,
                             b->stream));
     SweepArgs<T> sw = make_sweep_args<T>(b);
     sw.v = vtmp;
@@ -233,7 +199,7 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
     int ncol = b->ncolours;
     unsigned* bar = b->bar;
     if (damping && (!sw.colour_cells || !sw.cell_start || !sw.row_ptr || !sw.loc || !sw.w ||
-                    !sw.mass || !sw.minv || !sw.sumw || !sw.sumw2 || !sw.v || !cptr || !bar)) {
+                    !sw.mass || !sw.sumw || !sw.sumw2 || !sw.v || !cptr || !bar)) {
         set_error("damping sweep tables are not built");
         return SRDR_ERR_INVALID;
     }

@@ -8,14 +8,18 @@
 // they run concurrently and commute; the colours run one after another with
 // a bounded grid barrier in one cooperative launch.
 //
-// Mapping: one warp per block holds G cells, one group of L = 32/G lanes per
-// cell.  A group stages its cell's footprint velocities and inverse masses
-// (through L2: other SMs wrote them in earlier colour phases), the cell's CSR
-// rows and per-particle constants (read-only: cp.async, no register staging)
-// in shared memory, then updates the cell's particles one after another,
-// its lanes spread over each particle's neighbours.  More cells per warp give
-// each warp independent work to overlap the serial in-cell chain; fewer give
-// fewer shuffle levels per reduction.  G is chosen by the autotuner.
+// Mapping: a warp holds G cells, one group of L = 32/G lanes per cell.  A
+// group stages in shared memory its cell's CSR rows, weights and
+// per-particle constants (read-only, by cp.async) and its footprint's
+// velocity records (v, 1/m) (through L2: other SMs wrote them in earlier
+// colour phases), then updates the cell's particles one after another, its
+// lanes spread over each particle's neighbours.  The read-only part of the
+// group's next cell is requested before the grid barrier that precedes it,
+// so only the velocities are fetched after the barrier; inside the chain the
+// next particle's neighbour indices and weights are read while the current
+// particle's sums are reduced.  More cells per warp give each warp
+// independent work to overlap the serial in-cell chain; fewer give fewer
+// shuffle levels per reduction.  G is chosen by the autotuner.
 
 // ---------------------------------------------------------------- async copies
 __device__ inline void cp_async4(void* dst, const void* src)
@@ -138,17 +142,17 @@ __device__ inline bool grid_barrier(unsigned* count, volatile unsigned* gen, uns
 
 // ---------------------------------------------------------------- shared memory
 // Per cell (group):
-//   sv [D][F] footprint velocities, sminv [F] inverse masses, sw [P] weights,
-//   sm / s1 / s2 [C] mass, sum w, sum w^2 of the cell's particles,
+//   sv [F] footprint velocity records (vx, vy, vz, 1/m), sw [P] weights,
+//   sm / sbm / srd [C] per particle of the cell: mass, then (after staging)
+//   sum_B - m_i and 1 / ((sum_B - m_i)^2 + sum_B^2) (loaded as sum w, sum w^2),
 //   srow [C+1] absolute row starts, sl [P+4] footprint-local indices (uint16)
 template <typename T, int D>
 struct CellSmem {
-    T* sv;
-    T* sminv;
+    vec4_t<T>* sv;
     T* sw;
     T* sm;
-    T* s1;
-    T* s2;
+    T* sbm;
+    T* srd;
     int* srow;
     uint16_t* sl;
 };
@@ -156,7 +160,7 @@ struct CellSmem {
 template <typename T, int D>
 __host__ __device__ inline size_t cell_smem_bytes(int F, int P, int C)
 {
-    size_t b = sizeof(T) * ((size_t)(D + 1) * F + (size_t)P + 3 * (size_t)C);
+    size_t b = sizeof(T) * (4 * (size_t)F + (size_t)P + 3 * (size_t)C);
     b = (b + 3) & ~size_t(3);
     b += sizeof(int) * ((size_t)C + 1);
     b += sizeof(uint16_t) * ((size_t)P + 4);
@@ -167,13 +171,12 @@ template <typename T, int D>
 __device__ inline CellSmem<T, D> cell_smem(unsigned char* raw, int F, int P, int C)
 {
     CellSmem<T, D> s;
-    s.sv = reinterpret_cast<T*>(raw);
-    s.sminv = s.sv + (size_t)D * F;
-    s.sw = s.sminv + F;
+    s.sv = reinterpret_cast<vec4_t<T>*>(raw);
+    s.sw = reinterpret_cast<T*>(raw) + 4 * (size_t)F;
     s.sm = s.sw + P;
-    s.s1 = s.sm + C;
-    s.s2 = s.s1 + C;
-    size_t off = sizeof(T) * ((size_t)(D + 1) * F + (size_t)P + 3 * (size_t)C);
+    s.sbm = s.sm + C;
+    s.srd = s.sbm + C;
+    size_t off = sizeof(T) * (4 * (size_t)F + (size_t)P + 3 * (size_t)C);
     off = (off + 3) & ~size_t(3);
     s.srow = reinterpret_cast<int*>(raw + off);
     s.sl = reinterpret_cast<uint16_t*>(s.srow + C + 1);
@@ -189,133 +192,159 @@ __device__ inline T group_allsum(T x, unsigned gmask)
 }
 
 // ---------------------------------------------------------------- one cell
-template <typename T, int D, int L>
-__device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, const CellSmem<T, D>& s,
-                                  int gl, unsigned gmask)
-{
-    const int n = a.n;
-    const int cs = __ldg(a.cell_start + c), ce = __ldg(a.cell_start + c + 1);
-    const int np = ce - cs;
-    const int F = a.max_foot;
-    T* sv = s.sv;
-    T* sminv = s.sminv;
-    T* sw = s.sw;
-    const T cc = a.c;
+// What a group knows about its staged cell.
+struct CellStage {
+    int cs, np, p0, p1, my_off;
+    FootRuns fr;
+};
 
-    const FootRuns fr = foot_runs_group<L>(c, a.dim, a.nx, a.ny, a.nz, a.cell_start, gl, gmask);
-    const int Ftot = fr.total;
-    int my_off = 0;
+// Stage the read-only data of cell c: footprint runs, row starts, CSR weights
+// and footprint-local indices, masses and weight sums.  The copies are
+// asynchronous; run_cell waits for them.
+template <typename T, int D, int L>
+__device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellSmem<T, D>& s, int gl,
+                                       unsigned gmask)
+{
+    CellStage st;
+    st.cs = __ldg(a.cell_start + c);
+    const int ce = __ldg(a.cell_start + c + 1);
+    st.np = ce - st.cs;
+    st.fr = foot_runs_group<L>(c, a.dim, a.nx, a.ny, a.nz, a.cell_start, gl, gmask);
+    st.my_off = 0;
 #pragma unroll
     for (int r = 0; r < 9; ++r)
-        if (r < fr.nruns && cs >= fr.a[r] && cs < fr.a[r] + (fr.off[r + 1] - fr.off[r]))
-            my_off = fr.off[r] + (cs - fr.a[r]);
-    const int p0 = __ldg(a.row_ptr + cs), p1 = __ldg(a.row_ptr + ce);
-
-    // read-only data by asynchronous copies: CSR weights, footprint-local
-    // indices (as 32-bit words from an even start), rows, masses, sums
-    for (int k = p0 + gl; k < p1; k += L) cp_async_t(sw + (k - p0), a.w + k);
+        if (r < st.fr.nruns && st.cs >= st.fr.a[r] && st.cs < st.fr.a[r] + (st.fr.off[r + 1] - st.fr.off[r]))
+            st.my_off = st.fr.off[r] + (st.cs - st.fr.a[r]);
+    st.p0 = __ldg(a.row_ptr + st.cs);
+    st.p1 = __ldg(a.row_ptr + ce);
+    const int p0 = st.p0, p1 = st.p1, np = st.np;
+    for (int k = p0 + gl; k < p1; k += L) cp_async_t(s.sw + (k - p0), a.w + k);
     {
+        // footprint-local indices as 32-bit words from an even start
         const int w0 = p0 >> 1, w1 = (p1 + 1) >> 1;
         const uint32_t* lw = reinterpret_cast<const uint32_t*>(a.loc);
         uint32_t* sw32 = reinterpret_cast<uint32_t*>(s.sl);
         for (int k = w0 + gl; k < w1; k += L) cp_async4(sw32 + (k - w0), lw + k);
     }
-    for (int p = gl; p <= np; p += L) cp_async4(s.srow + p, a.row_ptr + cs + p);
+    for (int p = gl; p <= np; p += L) cp_async4(s.srow + p, a.row_ptr + st.cs + p);
     for (int p = gl; p < np; p += L) {
-        cp_async_t(s.sm + p, a.mass + cs + p);
-        cp_async_t(s.s1 + p, a.sumw + cs + p);
-        cp_async_t(s.s2 + p, a.sumw2 + cs + p);
+        cp_async_t(s.sm + p, a.mass + st.cs + p);
+        cp_async_t(s.sbm + p, a.sumw + st.cs + p);
+        cp_async_t(s.srd + p, a.sumw2 + st.cs + p);
     }
-    // velocities through L2 (ld.cg) and inverse masses, in register batches:
-    // every load of a batch is issued before its shared-memory stores
+    return st;
+}
+
+// Sweep the staged cell: fetch the footprint's velocity records, then the
+// local operators of its particles in order (backward: reverse order), then
+// write the footprint back.
+template <typename T, int D, int L>
+__device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int backward,
+                                const CellSmem<T, D>& s, int gl, unsigned gmask)
+{
+    using V4 = vec4_t<T>;
+    const int np = st.np, p0 = st.p0, my_off = st.my_off;
+    const int Ftot = st.fr.total;
+    V4* sv = s.sv;
+    const T* sw = s.sw;
+    const T cc = a.c;
+
+    // velocity records through L2, in register batches: every load of a
+    // batch is issued before its shared-memory stores
     constexpr int U = 16;
     for (int base = 0; base < Ftot; base += L * U) {
-        T tv[U][D], tm[U];
+        V4 tv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int q = base + u * L + gl;
-            if (q < Ftot) {
-                const int j = fr.particle(q);
-#pragma unroll
-                for (int d = 0; d < D; ++d) tv[u][d] = __ldcg(a.v + (size_t)d * n + j);
-                tm[u] = __ldg(a.minv + j);
-            }
+            if (q < Ftot) tv[u] = ldcg_v4<T>(a.v, st.fr.particle(q));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int q = base + u * L + gl;
-            if (q < Ftot) {
-#pragma unroll
-                for (int d = 0; d < D; ++d) sv[d * F + q] = tv[u][d];
-                sminv[q] = tm[u];
-            }
+            if (q < Ftot) sv[q] = tv[u];
         }
     }
     cp_async_wait_all();
     __syncwarp(gmask);
+    // per particle of the cell: sum_B - m_i and the local solve's denominator
+    for (int p = gl; p < np; p += L) {
+        const T mi = s.sm[p];
+        const T SB = cc * s.sbm[p];
+        const T SB2 = cc * cc * s.srd[p];
+        const T sbm = SB - mi;
+        s.sbm[p] = sbm;
+        s.srd[p] = T(1) / (sbm * sbm + SB2);
+    }
+    __syncwarp(gmask);
     const uint16_t* sl = s.sl + (p0 & 1);  // entry k at sl[k - p0]
 
-    for (int t = 0; t < np; ++t) {
-        const int p = backward ? np - 1 - t : t;
-        const int li = my_off + p;
-        const int k0 = s.srow[p] - p0, k1 = s.srow[p + 1] - p0;
-        if (!a.pairwise) {
-            const T mi = s.sm[p];
-            const T SB = cc * s.s1[p];
-            const T SB2 = cc * cc * s.s2[p];
-            T vi[D], E[D];
+    if (!a.pairwise) {
+        // E_i = -sum_j B_j (v_i - v_j), summed in the order of a 32-lane
+        // butterfly whatever L is: lane gl of the group keeps the 32/L
+        // "virtual lanes" gl + w L (neighbours k = virtual lane mod 32) and
+        // combines them as the first butterfly levels would, so the result
+        // does not depend on the cells-per-warp choice.  Rows of up to L*NK
+        // neighbours keep their indices and weights in registers, read for
+        // the next particle while the current one is reduced.
+        constexpr int V = 32 / L;
+        constexpr int NK = L == 32 ? 4 : (L == 16 ? 8 : 12);
+        int jj[NK];
+        T BB[NK];
+        int k0 = 0, k1 = 0;
+        auto slots = [&](int t, int (&j_)[NK], T (&b_)[NK], int& a0, int& a1) {
+            const int p = backward ? np - 1 - t : t;
+            a0 = s.srow[p] - p0;
+            a1 = s.srow[p + 1] - p0;
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                vi[d] = sv[d * F + li];
-                E[d] = 0;
+            for (int m = 0; m < NK; ++m) {
+                const int k = a0 + gl + m * L;
+                const bool ok = k < a1;
+                j_[m] = ok ? (int)sl[k] : my_off + p;
+                b_[m] = ok ? cc * sw[k] : T(0);
             }
-            // E_i = -sum_j B_j (v_i - v_j), summed in the order of a 32-lane
-            // butterfly whatever L is: lane gl of the group keeps the 32/L
-            // "virtual lanes" gl + w L (neighbours k = virtual lane mod 32)
-            // and combines them as the first butterfly levels would, so the
-            // result does not depend on the cells-per-warp choice.  Rows of up
-            // to L*NK neighbours keep their indices, weights and velocities in
-            // registers: every shared-memory load of the particle is issued
-            // before any of its stores.
-            constexpr int V = 32 / L;
-            constexpr int NK = L == 32 ? 4 : (L == 16 ? 8 : 12);
+        };
+        if (np > 0) slots(0, jj, BB, k0, k1);
+        for (int t = 0; t < np; ++t) {
+            const int p = backward ? np - 1 - t : t;
+            const int li = my_off + p;
+            const T sbm = s.sbm[p], rden = s.srd[p];
+            const V4 vi4 = sv[li];
+            const T vi[3] = {vi4.x, vi4.y, vi4.z};
+            const bool in_regs = k1 - k0 <= L * NK;
             T acc[V][D];
 #pragma unroll
             for (int w = 0; w < V; ++w)
 #pragma unroll
                 for (int d = 0; d < D; ++d) acc[w][d] = 0;
-            const bool in_regs = k1 - k0 <= L * NK;
-            int jj[NK];
-            T BB[NK], vj[NK][D], im[NK];
+            V4 vj[NK];
+            if (in_regs) {
+#pragma unroll
+                for (int m = 0; m < NK; ++m) vj[m] = sv[jj[m]];
+            }
+            // the next particle's slots (read-only data)
+            int jn[NK];
+            T Bn[NK];
+            int k0n = 0, k1n = 0;
+            if (t + 1 < np) slots(t + 1, jn, Bn, k0n, k1n);
             if (in_regs) {
 #pragma unroll
                 for (int m = 0; m < NK; ++m) {
-                    const int k = k0 + gl + m * L;
-                    const bool ok = k < k1;
-                    jj[m] = ok ? (int)sl[k] : li;
-                    BB[m] = ok ? cc * sw[k] : T(0);
+                    const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
+#pragma unroll
+                    for (int d = 0; d < D; ++d) acc[m % V][d] -= BB[m] * (vi[d] - vjd[d]);
                 }
-#pragma unroll
-                for (int m = 0; m < NK; ++m) {
-#pragma unroll
-                    for (int d = 0; d < D; ++d) vj[m][d] = sv[d * F + jj[m]];
-                    im[m] = sminv[jj[m]];
-                }
-#pragma unroll
-                for (int m = 0; m < NK; ++m)
-                    if (k0 + gl + m * L < k1)
-#pragma unroll
-                        for (int d = 0; d < D; ++d) acc[m % V][d] -= BB[m] * (vi[d] - vj[m][d]);
             } else {
                 for (int kb = k0 + gl; kb < k1; kb += 32) {
 #pragma unroll
                     for (int w = 0; w < V; ++w) {
                         const int k = kb + w * L;
                         if (k < k1) {
-                            const int j = sl[k];
+                            const V4 x = sv[sl[k]];
+                            const T xd[3] = {x.x, x.y, x.z};
                             const T B = cc * sw[k];
 #pragma unroll
-                            for (int d = 0; d < D; ++d) acc[w][d] -= B * (vi[d] - sv[d * F + j]);
+                            for (int d = 0; d < D; ++d) acc[w][d] -= B * (vi[d] - xd[d]);
                         }
                     }
                 }
@@ -329,47 +358,58 @@ __device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, co
 #pragma unroll
                         for (int d = 0; d < D; ++d) acc[w][d] = acc[w][d] + acc[w | sft][d];
             }
-#pragma unroll
-            for (int d = 0; d < D; ++d) E[d] = group_allsum<T, L>(acc[0][d], gmask);
             // k = E_i / ((sum B - m_i)^2 + sum B^2);  v_i += (sum B - m_i) k
-            const T sbm = SB - mi;
-            const T rden = T(1) / (sbm * sbm + SB2);
-            T kk[D], vin[D];
+            T kk[3] = {0, 0, 0}, vin[3] = {vi[0], vi[1], vi[2]};
 #pragma unroll
             for (int d = 0; d < D; ++d) {
-                kk[d] = E[d] * rden;
+                const T E = group_allsum<T, L>(acc[0][d], gmask);
+                kk[d] = E * rden;
                 vin[d] = vi[d] + sbm * kk[d];
             }
             // v_j <- v_j - B_j (v_i^new - v_j^p) / m_j,  v_j^p = v_j - B_j k
             if (in_regs) {
 #pragma unroll
                 for (int m = 0; m < NK; ++m)
-                    if (k0 + gl + m * L < k1)
+                    if (k0 + gl + m * L < k1) {
+                        const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
+                        T o[3] = {vjd[0], vjd[1], vjd[2]};
 #pragma unroll
                         for (int d = 0; d < D; ++d)
-                            sv[d * F + jj[m]] = vj[m][d] - BB[m] * (vin[d] - vj[m][d] + BB[m] * kk[d]) * im[m];
+                            o[d] = vjd[d] - BB[m] * (vin[d] - vjd[d] + BB[m] * kk[d]) * vj[m].w;
+                        sv[jj[m]] = V4{o[0], o[1], o[2], vj[m].w};
+                    }
             } else {
                 for (int k = k0 + gl; k < k1; k += L) {
                     const int j = sl[k];
                     const T B = cc * sw[k];
-                    const T imj = sminv[j];
+                    const V4 x = sv[j];
+                    const T xd[3] = {x.x, x.y, x.z};
+                    T o[3] = {xd[0], xd[1], xd[2]};
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        const T vjd = sv[d * F + j];
-                        sv[d * F + j] = vjd - B * (vin[d] - vjd + B * kk[d]) * imj;
-                    }
+                    for (int d = 0; d < D; ++d) o[d] = xd[d] - B * (vin[d] - xd[d] + B * kk[d]) * x.w;
+                    sv[j] = V4{o[0], o[1], o[2], x.w};
                 }
             }
             __syncwarp(gmask);
-            if (gl == 0) {
-#pragma unroll
-                for (int d = 0; d < D; ++d) sv[d * F + li] = vin[d];
-            }
+            if (gl == 0) sv[li] = V4{vin[0], vin[1], vin[2], vi4.w};
             __syncwarp(gmask);
-        } else {
-            // pairwise (Sec. 3.2): pairs in row order, then reversed, each
-            // solved in closed form (Eq. pairwise-solve) over half the step
-            if (gl == 0) {
+#pragma unroll
+            for (int m = 0; m < NK; ++m) {
+                jj[m] = jn[m];
+                BB[m] = Bn[m];
+            }
+            k0 = k0n;
+            k1 = k1n;
+        }
+    } else {
+        // pairwise (Sec. 3.2): for each particle, its pairs in row order,
+        // then reversed, each solved in closed form (Eq. pairwise-solve) over
+        // half the step
+        if (gl == 0) {
+            for (int t = 0; t < np; ++t) {
+                const int p = backward ? np - 1 - t : t;
+                const int li = my_off + p;
+                const int k0 = s.srow[p] - p0, k1 = s.srow[p + 1] - p0;
                 const T mi = s.sm[p];
                 const T ch = T(0.5) * cc;
                 for (int pass = 0; pass < 2; ++pass) {
@@ -377,27 +417,58 @@ __device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, co
                         const int k = pass == 0 ? k0 + t2 : k1 - 1 - t2;
                         const int j = sl[k];
                         const T B = ch * sw[k];
-                        const T mj = T(1) / sminv[j];
+                        V4 xi = sv[li], xj = sv[j];
+                        const T mj = T(1) / xj.w;
                         const T den = mi * mj - (mi + mj) * B;
+                        T pi_[3] = {xi.x, xi.y, xi.z}, pj_[3] = {xj.x, xj.y, xj.z};
 #pragma unroll
                         for (int d = 0; d < D; ++d) {
-                            const T vij = sv[d * F + li] - sv[d * F + j];
-                            sv[d * F + li] += mj * B * vij / den;
-                            sv[d * F + j] += -mi * B * vij / den;
+                            const T vij = pi_[d] - pj_[d];
+                            pi_[d] += mj * B * vij / den;
+                            pj_[d] += -mi * B * vij / den;
                         }
+                        sv[li] = V4{pi_[0], pi_[1], pi_[2], xi.w};
+                        sv[j] = V4{pj_[0], pj_[1], pj_[2], xj.w};
                     }
                 }
             }
-            __syncwarp(gmask);
         }
+        __syncwarp(gmask);
     }
     // write the footprint back (through L2: other SMs read it after the barrier)
-    for (int q = gl; q < Ftot; q += L) {
-        const int j = fr.particle(q);
-#pragma unroll
-        for (int d = 0; d < D; ++d) __stcg(a.v + (size_t)d * n + j, sv[d * F + q]);
-    }
+    for (int q = gl; q < Ftot; q += L) stcg_v4<T>(a.v, st.fr.particle(q), sv[q]);
     __syncwarp(gmask);
+}
+
+// Both stages back to back.
+template <typename T, int D, int L>
+__device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, const CellSmem<T, D>& s,
+                                  int gl, unsigned gmask)
+{
+    const CellStage st = stage_cell<T, D, L>(a, c, s, gl, gmask);
+    run_cell<T, D, L>(a, st, backward, s, gl, gmask);
+}
+
+// The first item of group q0 at or after phase ph (its first cell of that
+// phase), or -1 when there is none.
+__device__ inline int first_item(const int* __restrict__ colour_ptr, int ncolours, int ph, int q0)
+{
+    for (int p = ph; p < 2 * ncolours; ++p) {
+        const int c = p >= ncolours ? 2 * ncolours - 1 - p : p;
+        const int c0 = __ldg(colour_ptr + c), c1 = __ldg(colour_ptr + c + 1);
+        if (c0 + q0 < c1) return c0 + q0;
+    }
+    return -1;
+}
+
+// The item a group takes after item cid of phase ph: the next of the same
+// phase (stride qs), else its first of a later phase.
+__device__ inline int next_item(const int* __restrict__ colour_ptr, int ncolours, int ph, int cid, int q0,
+                                int qs)
+{
+    const int col = ph >= ncolours ? 2 * ncolours - 1 - ph : ph;
+    if (cid + qs < __ldg(colour_ptr + col + 1)) return cid + qs;
+    return first_item(colour_ptr, ncolours, ph + 1, q0);
 }
 
 // The whole S_d of one damped step in one cooperative launch: colours
@@ -419,15 +490,27 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
     const CellSmem<T, D> s = cell_smem<T, D>(smem_raw + (size_t)(wb * G + g) * cell_bytes, a.max_foot,
                                              a.max_pairs, a.max_cell);
     const int q0 = (blockIdx.x * W + wb) * G + g, qs = gridDim.x * W * G;
+    // the group's first cell, staged before the first phase
+    int staged = first_item(colour_ptr, ncolours, 0, q0);
+    CellStage st{};
+    if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
     int phases = 0;
     for (int ph = 0; ph < 2 * ncolours; ++ph) {
         const int backward = ph >= ncolours;
         const int col = backward ? 2 * ncolours - 1 - ph : ph;
         const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
         if (c1 == c0) continue;
-        if (phases++ > 0 && !grid_barrier(bar, bar + 1, gridDim.x, a.sc)) return;
-        for (int cid = c0 + q0; cid < c1; cid += qs)
-            sweep_cell<T, D, L>(a, __ldg(a.colour_cells + cid), backward, s, gl, gmask);
+        if (phases++ > 0 && !grid_barrier(bar, bar + 1, gridDim.x, a.sc)) {
+            cp_async_wait_all();  // no copy may land after the block has left
+            return;
+        }
+        for (int cid = c0 + q0; cid < c1; cid += qs) {
+            // staged == cid here: items are visited in the order next_item gives
+            run_cell<T, D, L>(a, st, backward, s, gl, gmask);
+            staged = next_item(colour_ptr, ncolours, ph, cid, q0, qs);
+            if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
+        }
         __syncwarp();
     }
+    cp_async_wait_all();
 }
