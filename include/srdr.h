@@ -154,6 +154,8 @@ typedef struct {
     int converged;         /* last relax met its criterion */
     int64_t launches;      /* kernels launched by step / relax calls since creation */
     int sweep_cells_per_warp; /* damping-sweep mapping picked by the autotuner (1, 2, 4) */
+    int pass_mapping;      /* mapping the stress and force passes use: SRDR_PASS_SELL or
+                              SRDR_PASS_BRICKS (SRDR_PASS_AUTO before the first step) */
 } srdr_stats;
 srdr_status srdr_body_stats(const srdr_body* body, srdr_stats* out);
 
@@ -190,6 +192,23 @@ srdr_status srdr_body_profile(srdr_body* body, int enable);
  * default).  The choice changes speed only: the sweep's sums follow one fixed
  * order, so results are bitwise the same. */
 srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp, int sweep_warps_per_block);
+
+/* Kernel mapping of the stress and force passes (Sec. 2.2-2.3 and the
+ * momentum equation).  SRDR_PASS_SELL: each thread streams its particle's
+ * neighbour row from a sliced-ELL layout and gathers the neighbours' data
+ * from global memory.  SRDR_PASS_BRICKS: one thread block per brick of
+ * brick_x x brick_y x brick_z cells stages the data of the brick's cell
+ * halo in shared memory and streams 16-bit halo indices; the layout is built
+ * on the first step after the call (brick sizes 1..4 cells, 0 = default
+ * 2 x 2 x 2 in 3D, 4 x 4 in 2D; SRDR_ERR_INVALID at that step if a brick's
+ * halo does not fit in shared memory).  SRDR_PASS_AUTO (the default): the
+ * sliced-ELL mapping, measured faster on GB300 for every body tried (the
+ * brick layout is then not built).  Both visit a row's neighbours in the
+ * same order with the same roundings, so results are bitwise the same; the
+ * choice changes speed only. */
+enum { SRDR_PASS_AUTO = 0, SRDR_PASS_SELL = 1, SRDR_PASS_BRICKS = 2 };
+srdr_status srdr_body_pass_mapping(srdr_body* body, int mapping, int brick_x, int brick_y,
+                                   int brick_z);
 srdr_status srdr_body_kernel_times(const srdr_body* body, srdr_kernel_times* out);
 
 void srdr_body_destroy(srdr_body* body);

@@ -306,9 +306,10 @@ __global__ void k_read_field(const int* __restrict__ perm, int n, int dim, const
             if (p < dim && q < dim) {
                 int k = p * dim + q;
                 if (aos_stride > 0) {
-                    // PB AoS layouts: 3D FP32 packs row-major in 12; 3D FP64 in 10;
-                    // 2D in 4 — all are plain row-major prefixes of the stride
-                    x = (double)src[(size_t)s * aos_stride + k];
+                    // PB: entry k in 16-byte chunk k / E (E = 16 / sizeof(T)
+                    // entries per chunk), chunk c of particle s at c n + s
+                    const int E = 16 / (int)sizeof(T);
+                    x = (double)src[((size_t)(k / E) * n + s) * E + k % E];
                 } else {
                     x = (double)src[(size_t)k * n + s];
                 }
@@ -524,6 +525,7 @@ srdr_status srdr_body_stats(const srdr_body* b, srdr_stats* out)
     out->converged = b->converged;
     out->launches = b->launches;
     out->sweep_cells_per_warp = b->sweep_cells_per_warp;
+    out->pass_mapping = b->pass_tiled < 0 ? SRDR_PASS_AUTO : (b->pass_tiled ? SRDR_PASS_BRICKS : SRDR_PASS_SELL);
     return SRDR_OK;
 }
 
@@ -544,6 +546,37 @@ srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp, int warps_per_block
         b->sweep_cells_per_warp = cells_per_warp;
         b->sweep_warps_per_block = warps_per_block;
     }
+    return SRDR_OK;
+}
+
+srdr_status srdr_body_pass_mapping(srdr_body* b, int mapping, int bx, int by, int bz)
+{
+    if (!b || mapping < SRDR_PASS_AUTO || mapping > SRDR_PASS_BRICKS || bx < 0 || bx > 4 || by < 0 ||
+        by > 4 || bz < 0 || bz > 4) {
+        set_error("pass mapping must be SRDR_PASS_AUTO, _SELL or _BRICKS with brick sizes 0..4");
+        return SRDR_ERR_INVALID;
+    }
+    const bool resize = bx != b->brick[0] || by != b->brick[1] || bz != b->brick[2];
+    if (resize && b->bricks_built != 0) {
+        // drop the old layout; the next step that needs bricks rebuilds it
+        for (void* p : {(void*)b->binfo, (void*)b->bown, (void*)b->bown_h, (void*)b->bhalo,
+                        (void*)b->bsell_ptr, (void*)b->blidx, b->bg, (void*)b->ke_pp})
+            SRDR_TRY(dev_free(b, p));
+        b->binfo = nullptr;
+        b->bown = nullptr;
+        b->bown_h = nullptr;
+        b->bhalo = nullptr;
+        b->bsell_ptr = nullptr;
+        b->blidx = nullptr;
+        b->bg = nullptr;
+        b->ke_pp = nullptr;
+        b->bricks_built = 0;
+    }
+    b->brick[0] = bx;
+    b->brick[1] = by;
+    b->brick[2] = bz;
+    b->pass_mapping = mapping;
+    b->pass_tiled = -1;
     return SRDR_OK;
 }
 

@@ -30,7 +30,7 @@ namespace srdr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 8;  // sliced-ELL slots per batch of loads in the passes
 
 #include "passes.cuh"
 #include "sweep.cuh"
@@ -122,8 +122,29 @@ __global__ void __launch_bounds__(kThreads) k_batch_ke(const BatchEntry<T>* __re
     ke_finalize(tab[b].step.ke_part, tab[b].nslices, sc, damp[b]);
 }
 
+// The next work item of a group at or after item k of phase ph (k < 0: from
+// the start of phase ph) that belongs to a damped body, and its phase; -1
+// when there is none.  Group q0 takes items q0, q0 + qs, ... of each colour.
+__device__ inline int batch_next(const int2* __restrict__ cells, const int* __restrict__ damp,
+                                 const int* __restrict__ colour_ptr, int ncolours, int ph, int k, int q0,
+                                 int qs, int* item_ph)
+{
+    for (int p = ph; p < 2 * ncolours; ++p) {
+        const int col = p >= ncolours ? 2 * ncolours - 1 - p : p;
+        const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
+        for (int kk = (p == ph && k >= 0) ? k + qs : c0 + q0; kk < c1; kk += qs)
+            if (damp[cells[kk].x]) {
+                *item_ph = p;
+                return kk;
+            }
+    }
+    return -1;
+}
+
 // S_d of every damped body: colour c of all bodies, then c+1, ...; forward
 // then backward; group g of block bb takes work items bb*G+g, +gridDim*G, ...
+// As in the single-body sweep, the read-only data of a group's next item is
+// staged between the barrier's arrive and wait.
 template <typename T, int D, int G>
 __global__ void __launch_bounds__(32) k_batch_sweep(const BatchEntry<T>* __restrict__ tab,
                                                     const int2* __restrict__ cells,
@@ -135,24 +156,56 @@ __global__ void __launch_bounds__(32) k_batch_sweep(const BatchEntry<T>* __restr
     constexpr int L = 32 / G;
     if (!*(volatile const int*)any) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned s_gen;
+    __shared__ int s_ok;
     const int g = threadIdx.x / L, gl = threadIdx.x % L;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
     const CellSmem<T, D> s =
         cell_smem<T, D>(smem_raw + (size_t)g * cell_smem_bytes<T, D>(F, P, C), F, P, C);
+    const int q0 = blockIdx.x * G + g, qs = gridDim.x * G;
+    int sph = 0;
+    int staged = batch_next(cells, damp, colour_ptr, ncolours, 0, -1, q0, qs, &sph);
+    CellStage st{};
+    if (staged >= 0) {
+        const int2 e = cells[staged];
+        st = stage_cell<T, D, L>(tab[e.x].sweep, e.y, s, gl, gmask);
+    }
+    bool restage = false;
     int phases = 0;
     for (int ph = 0; ph < 2 * ncolours; ++ph) {
         const int backward = ph >= ncolours;
         const int col = backward ? 2 * ncolours - 1 - ph : ph;
         const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
         if (c1 == c0) continue;
-        if (phases++ > 0 && !grid_barrier(bar, bar + 1, gridDim.x, status)) return;
-        for (int k = c0 + blockIdx.x * G + g; k < c1; k += gridDim.x * G) {
-            const int2 e = cells[k];
-            if (!damp[e.x]) continue;
-            sweep_cell<T, D, L>(tab[e.x].sweep, e.y, backward, s, gl, gmask);
+        if (phases++ > 0) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_gen = bar_arrive(bar, gridDim.x);
+            if (restage && staged >= 0) {
+                const int2 e = cells[staged];
+                st = stage_cell<T, D, L>(tab[e.x].sweep, e.y, s, gl, gmask);
+            }
+            restage = false;
+            if (threadIdx.x == 0) s_ok = bar_wait(bar, s_gen, status) ? 1 : 0;
+            __syncthreads();
+            if (!s_ok) {
+                cp_async_wait_all();  // no copy may land after the block has left
+                return;
+            }
+        }
+        while (staged >= 0 && sph == ph) {
+            const int2 e = cells[staged];
+            run_cell<T, D, L>(tab[e.x].sweep, st, backward, s, gl, gmask);
+            staged = batch_next(cells, damp, colour_ptr, ncolours, ph, staged, q0, qs, &sph);
+            if (staged >= 0 && sph == ph) {
+                const int2 e2 = cells[staged];
+                st = stage_cell<T, D, L>(tab[e2.x].sweep, e2.y, s, gl, gmask);
+            } else {
+                restage = true;
+            }
         }
         __syncwarp();
     }
+    cp_async_wait_all();
 }
 
 __global__ void k_batch_set_tol(DevScalars* const* scs, int nb, double tol)
@@ -684,7 +737,7 @@ srdr_status batch_create(srdr_body* const* bodies, int nb, void* stream, bool ow
     }
     if ((st = balloc_n(bt, &bt->damp, nb)) != SRDR_OK) return fail(st);
     if ((st = balloc_n(bt, &bt->any, 1)) != SRDR_OK) return fail(st);
-    if ((st = balloc_n(bt, &bt->bar, 2)) != SRDR_OK) return fail(st);
+    if ((st = balloc_n(bt, &bt->bar, kBarWords)) != SRDR_OK) return fail(st);
     if ((st = balloc_n(bt, &bt->status, 1)) != SRDR_OK) return fail(st);
     if ((st = balloc_n(bt, &bt->scs, nb)) != SRDR_OK) return fail(st);
     if ((st = balloc_n(bt, &bt->gathered, nb + 1)) != SRDR_OK) return fail(st);
@@ -697,7 +750,7 @@ srdr_status batch_create(srdr_body* const* bodies, int nb, void* stream, bool ow
     std::vector<DevScalars*> scs(nb);
     for (int b = 0; b < nb; ++b) scs[b] = bt->bodies[b]->sc;
     DevScalars z{};
-    if (cudaMemset(bt->bar, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
+    if (cudaMemset(bt->bar, 0, kBarWords * sizeof(unsigned)) != cudaSuccess ||
         cudaMemcpy(bt->status, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(bt->scs, scs.data(), sizeof(DevScalars*) * nb, cudaMemcpyHostToDevice) != cudaSuccess) {
         set_error("batch initialisation copies failed");

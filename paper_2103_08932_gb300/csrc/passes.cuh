@@ -1,77 +1,57 @@
 #include "pairg.cuh"
 
 // ------------------------------------------------------------------ layouts
-// u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 hi/lo float4 [n] each.
-// PB (P B0): AoS, padded to whole 16-byte vectors: stride pb_stride<T, D>.
+// u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 hi and lo arrays
+// [n][4] each (u = hi + lo).
+// PB (P B0): the D x D entries of a particle, row-major, in pb_chunks
+// 16-byte chunks; chunk c of all particles forms one dense array, chunk c of
+// particle j at 16-byte index c n + j.  A neighbour gather then reads one
+// 16-byte vector from each of a few dense arrays, so a warp's gathers touch
+// fewer cache lines than with a padded record per particle.
 template <typename T, int D>
-struct PBL;
-template <>
-struct PBL<float, 3> {
-    static constexpr int S = 12;
-    __device__ static void load(const float* p, int j, float (&m)[3][3])
+struct PBL {
+    static constexpr int C = pb_chunks(sizeof(T), D);
+    static constexpr int E = 16 / (int)sizeof(T);  // entries per chunk
+    __device__ static void load(const T* p, int n, int j, T (&m)[D][D])
     {
-        const float4* q = reinterpret_cast<const float4*>(p + (size_t)j * S);
-        float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-        m[0][0] = a.x; m[0][1] = a.y; m[0][2] = a.z;
-        m[1][0] = a.w; m[1][1] = b.x; m[1][2] = b.y;
-        m[2][0] = b.z; m[2][1] = b.w; m[2][2] = c.x;
+        T e[C * E];
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(p) + (size_t)c * n + j);
+                e[4 * c] = x.x;
+                e[4 * c + 1] = x.y;
+                e[4 * c + 2] = x.z;
+                e[4 * c + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const double2 x = __ldg(reinterpret_cast<const double2*>(p) + (size_t)c * n + j);
+                e[2 * c] = x.x;
+                e[2 * c + 1] = x.y;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int q = 0; q < D; ++q) m[r][q] = e[r * D + q];
     }
-    __device__ static void store(float* p, int j, const float (&m)[3][3])
+    __device__ static void store(T* p, int n, int j, const T (&m)[D][D])
     {
-        float4* q = reinterpret_cast<float4*>(p + (size_t)j * S);
-        q[0] = make_float4(m[0][0], m[0][1], m[0][2], m[1][0]);
-        q[1] = make_float4(m[1][1], m[1][2], m[2][0], m[2][1]);
-        q[2] = make_float4(m[2][2], 0.f, 0.f, 0.f);
-    }
-};
-template <>
-struct PBL<float, 2> {
-    static constexpr int S = 4;
-    __device__ static void load(const float* p, int j, float (&m)[2][2])
-    {
-        float4 a = __ldg(reinterpret_cast<const float4*>(p + (size_t)j * S));
-        m[0][0] = a.x; m[0][1] = a.y; m[1][0] = a.z; m[1][1] = a.w;
-    }
-    __device__ static void store(float* p, int j, const float (&m)[2][2])
-    {
-        *reinterpret_cast<float4*>(p + (size_t)j * S) = make_float4(m[0][0], m[0][1], m[1][0], m[1][1]);
-    }
-};
-template <>
-struct PBL<double, 3> {
-    static constexpr int S = 10;
-    __device__ static void load(const double* p, int j, double (&m)[3][3])
-    {
-        const double2* q = reinterpret_cast<const double2*>(p + (size_t)j * S);
-        double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3), e = __ldg(q + 4);
-        m[0][0] = a.x; m[0][1] = a.y; m[0][2] = b.x;
-        m[1][0] = b.y; m[1][1] = c.x; m[1][2] = c.y;
-        m[2][0] = d.x; m[2][1] = d.y; m[2][2] = e.x;
-    }
-    __device__ static void store(double* p, int j, const double (&m)[3][3])
-    {
-        double2* q = reinterpret_cast<double2*>(p + (size_t)j * S);
-        q[0] = make_double2(m[0][0], m[0][1]);
-        q[1] = make_double2(m[0][2], m[1][0]);
-        q[2] = make_double2(m[1][1], m[1][2]);
-        q[3] = make_double2(m[2][0], m[2][1]);
-        q[4] = make_double2(m[2][2], 0.0);
-    }
-};
-template <>
-struct PBL<double, 2> {
-    static constexpr int S = 4;
-    __device__ static void load(const double* p, int j, double (&m)[2][2])
-    {
-        const double2* q = reinterpret_cast<const double2*>(p + (size_t)j * S);
-        double2 a = __ldg(q), b = __ldg(q + 1);
-        m[0][0] = a.x; m[0][1] = a.y; m[1][0] = b.x; m[1][1] = b.y;
-    }
-    __device__ static void store(double* p, int j, const double (&m)[2][2])
-    {
-        double2* q = reinterpret_cast<double2*>(p + (size_t)j * S);
-        q[0] = make_double2(m[0][0], m[0][1]);
-        q[1] = make_double2(m[1][0], m[1][1]);
+        T e[C * E];
+#pragma unroll
+        for (int k = 0; k < C * E; ++k) e[k] = k < D * D ? m[k / D][k % D] : T(0);
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                reinterpret_cast<float4*>(p)[(size_t)c * n + j] =
+                    make_float4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                reinterpret_cast<double2*>(p)[(size_t)c * n + j] = make_double2(e[2 * c], e[2 * c + 1]);
+        }
     }
 };
 
@@ -115,8 +95,8 @@ struct UAcc<float> {
     __device__ static void load(const double*, const float* hi, const float* lo, int j, float (&h)[3],
                                 float (&l)[3])
     {
-        float4 a = __ldg(reinterpret_cast<const float4*>(hi) + j);
-        float4 b = __ldg(reinterpret_cast<const float4*>(lo) + j);
+        const float4 a = __ldg(reinterpret_cast<const float4*>(hi) + j);
+        const float4 b = __ldg(reinterpret_cast<const float4*>(lo) + j);
         h[0] = a.x; h[1] = a.y; h[2] = a.z;
         l[0] = b.x; l[1] = b.y; l[2] = b.z;
     }
@@ -238,10 +218,55 @@ __device__ inline void stress_PB(const T (&H)[D][D], const T (&B)[D][D], T lambd
 // ------------------------------------------------------------------ pass A
 // H_i = -(sum_j u_ij (x) g_ij) B0_i with g_ij = V_j grad0_i W_ij, i.e. the
 // corrected displacement gradient at u^{n+1/2}; F = I + H.
+//
+// The per-neighbour accumulations use explicit roundings (no contraction
+// left to the compiler), so the sliced-ELL kernels and the brick-tiled
+// kernels, which visit a row's neighbours in the same order, give the same
+// bits.
+__device__ inline float fma_t(float x, float y, float z) { return __fmaf_rn(x, y, z); }
+__device__ inline double fma_t(double x, double y, double z) { return __fma_rn(x, y, z); }
+__device__ inline float sub_t(float x, float y) { return __fsub_rn(x, y); }
+__device__ inline double sub_t(double x, double y) { return __dsub_rn(x, y); }
+
+// G += (u_i - u_j) (x) g_ij
+template <typename T, int D>
+__device__ inline void acc_grad(T (&G)[D][D], const T (&xi)[3], const T (&li)[3], const T (&xj)[3],
+                                const T (&lj)[3], const T (&g)[D])
+{
+#pragma unroll
+    for (int p = 0; p < D; ++p) {
+        const T du = UAcc<T>::diff(xi, li, xj, lj, p);
+#pragma unroll
+        for (int q = 0; q < D; ++q) G[p][q] = fma_t(du, g[q], G[p][q]);
+    }
+}
+
+// H = -G B0, stress, P B0 stored
+template <typename T, int D, int MAT>
+__device__ inline void pass_a_epilogue(const StepArgs<T>& a, int i, const T (&G)[D][D])
+{
+    const int n = a.n;
+    T B[D][D], H[D][D], PB[D][D];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) B[p][q] = a.B0[(size_t)(p * D + q) * n + i];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            T s2 = 0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) s2 += G[p][r] * B[r][q];
+            H[p][q] = -s2;
+        }
+    stress_PB<T, D, MAT>(H, B, a.lambda, a.mu, PB);
+    PBL<T, D>::store(a.PB, n, i, PB);
+}
+
 template <typename T, int D, int MAT>
 __device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
 {
-    const int n = a.n;
     int s = i >> 5, lane = i & 31;
     int base = __ldg(a.sell_ptr + s);
     int width = (__ldg(a.sell_ptr + s + 1) - base) >> 5;
@@ -271,30 +296,9 @@ __device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) UAcc<T>::load(a.u, a.uhi, a.ulo, jj[u], xj[u], lj[u]);
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-            for (int p = 0; p < D; ++p) {
-                T du = UAcc<T>::diff(xi, li, xj[u], lj[u], p);
-#pragma unroll
-                for (int q = 0; q < D; ++q) G[p][q] += du * gg[u][q];
-            }
+        for (int u = 0; u < kUnroll; ++u) acc_grad<T, D>(G, xi, li, xj[u], lj[u], gg[u]);
     }
-    T B[D][D], H[D][D], PB[D][D];
-#pragma unroll
-    for (int p = 0; p < D; ++p)
-#pragma unroll
-        for (int q = 0; q < D; ++q) B[p][q] = a.B0[(size_t)(p * D + q) * n + i];
-#pragma unroll
-    for (int p = 0; p < D; ++p)
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-            T s2 = 0;
-#pragma unroll
-            for (int r = 0; r < D; ++r) s2 += G[p][r] * B[r][q];
-            H[p][q] = -s2;
-        }
-    stress_PB<T, D, MAT>(H, B, a.lambda, a.mu, PB);
-    PBL<T, D>::store(a.PB, i, PB);
+    pass_a_epilogue<T, D, MAT>(a, i, G);
 }
 
 template <typename T, int D, int MAT>
@@ -405,78 +409,93 @@ __device__ inline void u_add<float>(const StepArgs<float>& a, int i, const float
 // (1/rho0) [ sum_j (PB_j - PB_i) g_ij + 2 PB_i G_i ] + g with G_i = sum_j g_ij,
 // the same sum written without the cancellation of a nearly uniform stress.
 // Then v* = v^n + dt dv/dt (constrained: v = 0); on an undamped step also
-// u^{n+3/2} = u^{n+1/2} + dt v^{n+1} and the KE partials.
+// u^{n+3/2} = u^{n+1/2} + dt v^{n+1} and the particle's kinetic energy.
+
+// acc += (PB_j - PB_i) g_ij
 template <typename T, int D>
-__device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_step)
+__device__ inline void acc_force(T (&acc)[D], const T (&Pi)[D][D], const T (&Pj)[D][D], const T (&g)[D])
+{
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) acc[p] = fma_t(sub_t(Pj[p][q], Pi[p][q]), g[q], acc[p]);
+}
+
+// the 2 PB_i G_i term, velocity update and constraints, and on an undamped
+// step the displacement update; returns the particle's kinetic energy (0 if
+// not final or constrained)
+template <typename T, int D>
+__device__ inline double pass_b_epilogue(const StepArgs<T>& a, int i, T (&acc)[D], const T (&Pi)[D][D],
+                                         int final_step)
 {
     const int n = a.n;
     double ke = 0.0;
-    {
-        int s = i >> 5, lane = i & 31;
-        int base = __ldg(a.sell_ptr + s);
-        int width = (__ldg(a.sell_ptr + s + 1) - base) >> 5;
-        T Pi[D][D];
-        PBL<T, D>::load(a.PB, i, Pi);
-        T acc[D];
+    T Gi[D];
 #pragma unroll
-        for (int p = 0; p < D; ++p) acc[p] = 0;
-        for (int t0 = 0; t0 < width; t0 += kUnroll) {
-            int jj[kUnroll];
-            T gg[kUnroll][D];
+    for (int q = 0; q < D; ++q) Gi[q] = a.Gs[(size_t)q * n + i];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int k = base + (t0 + u) * 32 + lane;
-                const bool in = t0 + u < width;
-                jj[u] = in ? __ldg(a.sell_col + k) : i;
-                gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
-                gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
-                if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
-            }
-            T Pj[kUnroll][D][D];
+    for (int p = 0; p < D; ++p)
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, jj[u], Pj[u]);
+        for (int q = 0; q < D; ++q) acc[p] += T(2) * Pi[p][q] * Gi[q];
+    uint8_t f = a.flags[i];
+    vec4_t<T> v4 = ld_v4<T>(a.v, i);
+    T vi[3] = {v4.x, v4.y, v4.z};
+    if (f & SRDR_FLAG_CONSTRAINED) {
+        vi[0] = vi[1] = vi[2] = 0;
+    } else {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-                for (int p = 0; p < D; ++p)
-#pragma unroll
-                    for (int q = 0; q < D; ++q) acc[p] += (Pj[u][p][q] - Pi[p][q]) * gg[u][q];
+        for (int p = 0; p < D; ++p) {
+            T ap = acc[p] * a.inv_rho0 + a.grav[p];
+            if (f & SRDR_FLAG_END_LOAD) ap += a.endl[p];
+            vi[p] += a.dt * ap;
         }
-        T Gi[D];
-#pragma unroll
-        for (int q = 0; q < D; ++q) Gi[q] = a.Gs[(size_t)q * n + i];
-#pragma unroll
-        for (int p = 0; p < D; ++p)
-#pragma unroll
-            for (int q = 0; q < D; ++q) acc[p] += T(2) * Pi[p][q] * Gi[q];
-        uint8_t f = a.flags[i];
-        vec4_t<T> v4 = ld_v4<T>(a.v, i);
-        T vi[3] = {v4.x, v4.y, v4.z};
-        if (f & SRDR_FLAG_CONSTRAINED) {
-            vi[0] = vi[1] = vi[2] = 0;
-        } else {
-#pragma unroll
-            for (int p = 0; p < D; ++p) {
-                T ap = acc[p] * a.inv_rho0 + a.grav[p];
-                if (f & SRDR_FLAG_END_LOAD) ap += a.endl[p];
-                vi[p] += a.dt * ap;
-            }
-        }
-        v4.x = vi[0];
-        v4.y = vi[1];
-        v4.z = vi[2];
-        st_v4<T>(a.v, i, v4);
-        if (final_step && !(f & SRDR_FLAG_CONSTRAINED)) {
-            T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
-            u_add<T>(a, i, d);
-            ke = ke_particle<T>(a.mass[i], vi);
-        }
+    }
+    v4.x = vi[0];
+    v4.y = vi[1];
+    v4.z = vi[2];
+    st_v4<T>(a.v, i, v4);
+    if (final_step && !(f & SRDR_FLAG_CONSTRAINED)) {
+        T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
+        u_add<T>(a, i, d);
+        ke = ke_particle<T>(a.mass[i], vi);
     }
     return ke;
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kThreads) k_pass_b(StepArgs<T> a, int final_step)
+__device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_step)
+{
+    int s = i >> 5, lane = i & 31;
+    int base = __ldg(a.sell_ptr + s);
+    int width = (__ldg(a.sell_ptr + s + 1) - base) >> 5;
+    T Pi[D][D];
+    PBL<T, D>::load(a.PB, a.n, i, Pi);
+    T acc[D];
+#pragma unroll
+    for (int p = 0; p < D; ++p) acc[p] = 0;
+    for (int t0 = 0; t0 < width; t0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int k = base + (t0 + u) * 32 + lane;
+            const bool in = t0 + u < width;
+            jj[u] = in ? __ldg(a.sell_col + k) : i;
+            gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
+            gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
+            if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
+        }
+        T Pj[kUnroll][D][D];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, a.n, jj[u], Pj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) acc_force<T, D>(acc, Pi, Pj[u], gg[u]);
+    }
+    return pass_b_epilogue<T, D>(a, i, acc, Pi, final_step);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads, 3) k_pass_b(StepArgs<T> a, int final_step)
 {
     if (a.sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -732,8 +732,8 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     b->max_foot = hfs[0];
     b->max_pairs = hfs[1];
     b->max_cell = hfs[2];
-    SRDR_TRY(dalloc(b, &b->bar, 2));
-    SRDR_CK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * 2, st));
+    SRDR_TRY(dalloc(b, &b->bar, kBarWords));
+    SRDR_CK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * kBarWords, st));
     if (b->max_foot >= 65536) {
         set_error("a cell footprint holds %d particles (limit 65535)", b->max_foot);
         return SRDR_ERR_INVALID;
@@ -765,6 +765,278 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     return SRDR_OK;
 }
 
+
+// ------------------------------------------------------------------ brick tiles
+// Bricks of bx x by x bz cells tile the cell grid (brick q = qx + nbx (qy +
+// nby qz)).  A brick's own particles are those of its cells, in rows of
+// cells along x (z outer, y inner), each row a contiguous range of sorted
+// particles; its halo is the box of cells one cell wider on every side
+// (clipped to the grid), again as rows.  Every neighbour of an own particle
+// lies in the halo.
+constexpr int kMaxHaloRows = 36;  // (4 + 2) x (4 + 2)
+
+struct BrickGeo {
+    int x0, x1, y0, y1, z0, z1;        // own cell box (inclusive)
+    int hx0, hx1, hy0, hy1, hz0, hz1;  // halo cell box (inclusive)
+};
+
+__device__ inline BrickGeo brick_geo(int q, const int* bd, const int* nb, int nx, int ny, int nz)
+{
+    BrickGeo g;
+    const int qx = q % nb[0], qy = (q / nb[0]) % nb[1], qz = q / (nb[0] * nb[1]);
+    g.x0 = qx * bd[0];
+    g.x1 = min(g.x0 + bd[0], nx) - 1;
+    g.y0 = qy * bd[1];
+    g.y1 = min(g.y0 + bd[1], ny) - 1;
+    g.z0 = qz * bd[2];
+    g.z1 = min(g.z0 + bd[2], nz) - 1;
+    g.hx0 = max(g.x0 - 1, 0);
+    g.hx1 = min(g.x1 + 1, nx - 1);
+    g.hy0 = max(g.y0 - 1, 0);
+    g.hy1 = min(g.y1 + 1, ny - 1);
+    g.hz0 = max(g.z0 - 1, 0);
+    g.hz1 = min(g.z1 + 1, nz - 1);
+    return g;
+}
+
+struct BrickDims {
+    int bd[3], nb[3];
+};
+
+__global__ void k_brick_count(const int* __restrict__ start, int nx, int ny, int nz, BrickDims d, int nball,
+                              int* __restrict__ nown, int* __restrict__ nhalo)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nball) return;
+    const BrickGeo g = brick_geo(q, d.bd, d.nb, nx, ny, nz);
+    int own = 0, halo = 0;
+    for (int z = g.z0; z <= g.z1; ++z)
+        for (int y = g.y0; y <= g.y1; ++y)
+            own += start[g.x1 + nx * (y + ny * z) + 1] - start[g.x0 + nx * (y + ny * z)];
+    for (int z = g.hz0; z <= g.hz1; ++z)
+        for (int y = g.hy0; y <= g.hy1; ++y)
+            halo += start[g.hx1 + nx * (y + ny * z) + 1] - start[g.hx0 + nx * (y + ny * z)];
+    nown[q] = own;
+    nhalo[q] = halo;
+}
+
+// halo rows of a brick: first sorted particle hst[r] and halo offset hoff[r]
+struct HaloRows {
+    int nr, hny;
+    int hst[kMaxHaloRows];
+    int hoff[kMaxHaloRows + 1];
+};
+
+__device__ inline void halo_rows(const BrickGeo& g, const int* start, int nx, int ny, HaloRows& h)
+{
+    h.hny = g.hy1 - g.hy0 + 1;
+    h.nr = 0;
+    h.hoff[0] = 0;
+    for (int z = g.hz0; z <= g.hz1; ++z)
+        for (int y = g.hy0; y <= g.hy1; ++y) {
+            const int a = start[g.hx0 + nx * (y + ny * z)], e = start[g.hx1 + nx * (y + ny * z) + 1];
+            h.hst[h.nr] = a;
+            h.hoff[h.nr + 1] = h.hoff[h.nr] + (e - a);
+            ++h.nr;
+        }
+}
+
+// bown / bown_h (own particles in brick order and their halo indices) and
+// bhalo (halo particles), one block per non-empty brick
+__global__ void k_brick_fill(const BrickInfo* __restrict__ info, const int* __restrict__ start, int nx,
+                             int ny, int nz, BrickDims d, int* __restrict__ bown,
+                             uint16_t* __restrict__ bown_h, int* __restrict__ bhalo)
+{
+    __shared__ HaloRows h;
+    const BrickInfo bi = info[blockIdx.x];
+    const BrickGeo g = brick_geo(bi.q, d.bd, d.nb, nx, ny, nz);
+    if (threadIdx.x == 0) halo_rows(g, start, nx, ny, h);
+    __syncthreads();
+    for (int r = 0; r < h.nr; ++r)
+        for (int e = threadIdx.x; e < h.hoff[r + 1] - h.hoff[r]; e += blockDim.x)
+            bhalo[bi.halo_base + h.hoff[r] + e] = h.hst[r] + e;
+    int ko = 0;
+    for (int z = g.z0; z <= g.z1; ++z)
+        for (int y = g.y0; y <= g.y1; ++y) {
+            const int a = start[g.x0 + nx * (y + ny * z)], e = start[g.x1 + nx * (y + ny * z) + 1];
+            const int r = (z - g.hz0) * h.hny + (y - g.hy0);
+            for (int t = threadIdx.x; t < e - a; t += blockDim.x) {
+                bown[bi.own_base + ko + t] = a + t;
+                bown_h[bi.own_base + ko + t] = (uint16_t)(h.hoff[r] + (a + t - h.hst[r]));
+            }
+            ko += e - a;
+        }
+}
+
+// slots of each brick slice (32 own particles): 32 x the longest row
+__global__ void k_bslice_width(const BrickInfo* __restrict__ info, const int* __restrict__ bown,
+                               const int* __restrict__ row_ptr, int* __restrict__ slots)
+{
+    const BrickInfo bi = info[blockIdx.x];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ns = (bi.nown + 31) >> 5;
+    for (int sl = w; sl < ns; sl += blockDim.x >> 5) {
+        const int k = sl * 32 + lane;
+        int deg = 0;
+        if (k < bi.nown) {
+            const int i = bown[bi.own_base + k];
+            deg = row_ptr[i + 1] - row_ptr[i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) deg = max(deg, __shfl_xor_sync(0xffffffffu, deg, o));
+        if (lane == 0) slots[bi.slice_base + sl] = deg * 32;
+    }
+}
+
+// brick sliced ELL: slot (slice, column t, lane) holds the halo index of
+// neighbour t of the lane's own particle and g_ij (the formula of the
+// sliced-ELL layout, so both layouts hold the same bits); padding: the
+// particle itself (lanes past the brick's particles: index 0) with g = 0
+template <typename T, int D>
+__global__ void k_bsell_fill(const BrickInfo* __restrict__ info, const int* __restrict__ start, int nx,
+                             int ny, int nz, BrickDims d, const int* __restrict__ bown,
+                             const uint16_t* __restrict__ bown_h, const int* __restrict__ row_ptr,
+                             const int* __restrict__ col, const int* __restrict__ cell_of,
+                             const int* __restrict__ bsell_ptr, const T* __restrict__ cpos,
+                             const int* __restrict__ ccell, T rc, T inv_h, T kc,
+                             uint16_t* __restrict__ lidx, T* __restrict__ sg, int64_t nslots)
+{
+    __shared__ HaloRows h;
+    const BrickInfo bi = info[blockIdx.x];
+    const BrickGeo g = brick_geo(bi.q, d.bd, d.nb, nx, ny, nz);
+    if (threadIdx.x == 0) halo_rows(g, start, nx, ny, h);
+    __syncthreads();
+    const int ns = (bi.nown + 31) >> 5;
+    for (int k = threadIdx.x; k < ns * 32; k += blockDim.x) {
+        const int sl = bi.slice_base + (k >> 5), lane = k & 31;
+        const int base = bsell_ptr[sl], width = (bsell_ptr[sl + 1] - base) >> 5;
+        const bool own = k < bi.nown;
+        int i = 0, hi = 0, k0 = 0, deg = 0;
+        vec4_t<T> pi{};
+        int ci = 0;
+        if (own) {
+            i = bown[bi.own_base + k];
+            hi = bown_h[bi.own_base + k];
+            k0 = row_ptr[i];
+            deg = row_ptr[i + 1] - k0;
+            pi = load_cpos<T>(cpos, i);
+            ci = ccell[i];
+        }
+        for (int t = 0; t < width; ++t) {
+            const int64_t slot = (int64_t)base + t * 32 + lane;
+            T gq[3] = {0, 0, 0};
+            int l = hi;
+            if (t < deg) {
+                const int j = col[k0 + t];
+                const int c = cell_of[j];
+                const int cy = (c / nx) % ny, cz = c / (nx * ny);
+                const int r = (cz - g.hz0) * h.hny + (cy - g.hy0);
+                l = h.hoff[r] + (j - h.hst[r]);
+                T gg[D];
+                PairG<T>::template g<D>(pi, ci, load_cpos<T>(cpos, j), ccell[j], rc, inv_h, kc, gg);
+                for (int q = 0; q < D; ++q) gq[q] = gg[q];
+            }
+            lidx[slot] = (uint16_t)l;
+            for (int q = 0; q < 3; ++q) sg[(size_t)q * nslots + slot] = gq[q];
+        }
+    }
+}
+
+template <typename T>
+srdr_status build_bricks_typed(srdr_body* b)
+{
+    cudaStream_t st = b->stream;
+    const int dim = b->dim;
+    BrickDims d;
+    for (int a = 0; a < 3; ++a) {
+        int e = b->brick[a];
+        if (e == 0) e = dim == 2 ? (a < 2 ? 4 : 1) : 2;
+        if (a >= dim) e = 1;
+        d.bd[a] = e;
+        d.nb[a] = (b->nc[a] + e - 1) / e;
+    }
+    const int nball = d.nb[0] * d.nb[1] * d.nb[2];
+    int *nown_d = nullptr, *nhalo_d = nullptr;
+    SRDR_TRY(dalloc(b, &nown_d, nball));
+    SRDR_TRY(dalloc(b, &nhalo_d, nball));
+    k_brick_count<<<nblocks(nball), kThreads, 0, st>>>(b->cell_start, b->nc[0], b->nc[1], b->nc[2], d, nball,
+                                                       nown_d, nhalo_d);
+    std::vector<int> nown(nball), nhalo(nball);
+    SRDR_CK(cudaMemcpyAsync(nown.data(), nown_d, sizeof(int) * nball, cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaMemcpyAsync(nhalo.data(), nhalo_d, sizeof(int) * nball, cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    SRDR_TRY(dev_free(b, nown_d));
+    SRDR_TRY(dev_free(b, nhalo_d));
+    std::vector<BrickInfo> info;
+    int64_t own = 0, halo = 0, slices = 0;
+    int max_halo = 0, max_own = 0;
+    for (int q = 0; q < nball; ++q) {
+        if (nown[q] == 0) continue;
+        BrickInfo bi{q, (int)own, (int)halo, (int)slices, nown[q], nhalo[q], 0, 0};
+        info.push_back(bi);
+        own += nown[q];
+        halo += nhalo[q];
+        slices += (nown[q] + 31) / 32;
+        max_halo = std::max(max_halo, nhalo[q]);
+        max_own = std::max(max_own, nown[q]);
+    }
+    const size_t smem = std::max(tile_smem_a(sizeof(T), max_halo), tile_smem_b(sizeof(T), dim, max_halo));
+    if (own != b->n || halo > 0x7fffffffLL || max_halo >= 65536 || smem > kTileSmemMax) {
+        b->bricks_built = -1;
+        return SRDR_OK;
+    }
+    b->nbricks = (int)info.size();
+    b->max_halo = max_halo;
+    b->max_own = max_own;
+    b->nbslices = (int)slices;
+    SRDR_TRY(dalloc(b, &b->binfo, info.size()));
+    SRDR_CK(cudaMemcpyAsync(b->binfo, info.data(), sizeof(BrickInfo) * info.size(), cudaMemcpyHostToDevice,
+                            st));
+    SRDR_TRY(dalloc(b, &b->bown, b->n));
+    SRDR_TRY(dalloc(b, &b->bown_h, b->n));
+    SRDR_TRY(dalloc(b, &b->bhalo, std::max<int64_t>(halo, 1)));
+    const int nbk = b->nbricks;
+    k_brick_fill<<<nbk, 128, 0, st>>>(b->binfo, b->cell_start, b->nc[0], b->nc[1], b->nc[2], d, b->bown,
+                                      b->bown_h, b->bhalo);
+    int *slots = nullptr, *tmp = nullptr;
+    SRDR_TRY(dalloc(b, &slots, std::max<int64_t>(slices, 1)));
+    SRDR_TRY(dalloc(b, &tmp, (slices + 1) / kScanBlock + 4));
+    SRDR_TRY(dalloc(b, &b->bsell_ptr, slices + 1));
+    k_bslice_width<<<nbk, 128, 0, st>>>(b->binfo, b->bown, b->row_ptr, slots);
+    SRDR_TRY(scan_exclusive(slots, b->bsell_ptr, (int)slices, tmp, st));
+    int nslots = 0;
+    SRDR_CK(cudaMemcpyAsync(&nslots, b->bsell_ptr + slices, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    if (nslots < 0) {
+        set_error("brick sliced-ELL layout exceeds 2^31 slots");
+        return SRDR_ERR_INVALID;
+    }
+    const int64_t ns = std::max(nslots, 1);
+    b->bslots = ns;
+    T* sg = nullptr;
+    SRDR_TRY(dalloc(b, &b->blidx, ns));
+    SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
+    b->bg = sg;
+    const T rcT = (T)b->rc, ihT = (T)(1.0 / b->h), kcT = (T)kernel_kc(dim, b->h);
+    if (dim == 2)
+        k_bsell_fill<T, 2><<<nbk, 128, 0, st>>>(b->binfo, b->cell_start, b->nc[0], b->nc[1], b->nc[2], d,
+                                                b->bown, b->bown_h, b->row_ptr, b->col, b->cell_of,
+                                                b->bsell_ptr, static_cast<const T*>(b->cpos), b->ccell, rcT,
+                                                ihT, kcT, b->blidx, sg, ns);
+    else
+        k_bsell_fill<T, 3><<<nbk, 128, 0, st>>>(b->binfo, b->cell_start, b->nc[0], b->nc[1], b->nc[2], d,
+                                                b->bown, b->bown_h, b->row_ptr, b->col, b->cell_of,
+                                                b->bsell_ptr, static_cast<const T*>(b->cpos), b->ccell, rcT,
+                                                ihT, kcT, b->blidx, sg, ns);
+    SRDR_CK(cudaGetLastError());
+    SRDR_TRY(dalloc(b, &b->ke_pp, b->n));
+    SRDR_CK(cudaStreamSynchronize(st));
+    SRDR_TRY(dev_free(b, slots));
+    SRDR_TRY(dev_free(b, tmp));
+    b->bricks_built = 1;
+    return SRDR_OK;
+}
+
 }  // namespace
 
 srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* vol,
@@ -777,6 +1049,17 @@ srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* 
     b->n = n;
     if (b->prec == SRDR_FP64) return build_typed<double>(b, n, r0, vol, flags, u0);
     return build_typed<float>(b, n, r0, vol, flags, u0);
+}
+
+srdr_status build_bricks(srdr_body* b)
+{
+    for (int a = 0; a < 3; ++a)
+        if (b->brick[a] < 0 || b->brick[a] > 4) {
+            set_error("brick size must be 1..4 cells (0: default)");
+            return SRDR_ERR_INVALID;
+        }
+    if (b->prec == SRDR_FP64) return build_bricks_typed<double>(b);
+    return build_bricks_typed<float>(b);
 }
 
 }  // namespace srdr

@@ -11,7 +11,7 @@
 //   v     T [n][4] velocity records (vx, vy, vz, 1/m): one 16-byte (FP32) or
 //         two 16-byte (FP64) accesses per particle
 //   B0    T [D*D][n] row-major tensor components, SoA (read by the owner only)
-//   PB    T [n][pb_stride] AoS padded to 16-byte vectors (gathered)
+//   PB    T [pb_chunks][n] 16-byte chunks of the row-major entries (gathered)
 //   G     T [3][n]   sum_j V_j grad W_ij (for the difference form of the force)
 //   CSR   row_ptr int32 [n+1], col int32 [nnz] (sorted ids, ascending),
 //         loc uint16 [nnz] (index of j inside the 3^d-cell footprint of
@@ -63,6 +63,18 @@ struct DevScalars {
     long long err_index;   // first offending particle / cell for status
 };
 
+// grid-barrier buffer: kBarSub arrival sub-counters, a top counter and a
+// generation word, each on its own 128-byte line
+constexpr int kBarSub = 32;
+constexpr int kBarWords = 32 * (kBarSub + 2);
+
+// One brick of the tiled passes: its index in the brick grid, the offsets of
+// its own particles (brick order), halo list and brick-sliced-ELL slices,
+// and its particle counts.
+struct BrickInfo {
+    int q, own_base, halo_base, slice_base, nown, nhalo, pad0, pad1;
+};
+
 // device error codes written to DevScalars::status
 enum { DEV_OK = 0, DEV_SINGULAR_B0 = 1, DEV_NONFINITE = 2, DEV_TIMEOUT = 3 };
 
@@ -77,12 +89,12 @@ struct StepArgs {
     const T* __restrict__ cpos;   // [n][4] offset in its cell (x, y, z) and volume
     const int* __restrict__ ccell; // [n] packed cell coordinates x | y << 10 | z << 20
     const T* __restrict__ B0;   // [D*D][n]
-    T* __restrict__ PB;         // [n][pb_stride]
+    T* __restrict__ PB;         // [pb_chunks][n] 16-byte chunks
     const T* __restrict__ Gs;   // [3][n]
     T* __restrict__ v;          // [n][4] (vx, vy, vz, 1/m)
     double* __restrict__ u;     // [3][n] FP64 mode
-    float* __restrict__ uhi;    // [3][n] FP32 mode
-    float* __restrict__ ulo;    // [3][n] FP32 mode
+    float* __restrict__ uhi;    // [n][4] FP32 mode, u = hi + lo
+    float* __restrict__ ulo;    // [n][4] FP32 mode
     const uint8_t* __restrict__ flags;
     const T* __restrict__ mass;
     double* __restrict__ ke_part;
@@ -158,10 +170,10 @@ struct srdr_body {
     void* Gs = nullptr;         // T [3][n]
     void* sumw = nullptr;
     void* sumw2 = nullptr;
-    void* v = nullptr;          // T [3][n]
+    void* v = nullptr;          // T [n][4] (vx, vy, vz, 1/m)
     double* u = nullptr;        // FP64 [3][n]
-    float* uhi = nullptr;
-    float* ulo = nullptr;
+    float* uhi = nullptr;       // [n][4] FP32 mode
+    float* ulo = nullptr;       // [n][4] FP32 mode
     double* ke_part = nullptr;
     int ke_blocks = 0;
     srdr::DevScalars* sc = nullptr;
@@ -170,7 +182,22 @@ struct srdr_body {
     int pb_stride = 0;               // T elements per particle in PB
     int max_foot = 0, max_pairs = 0, max_cell = 0;  // per-cell maxima
     int* colour_ptr_d = nullptr;     // device copy of colour_ptr
-    unsigned* bar = nullptr;         // grid-barrier count and generation
+    unsigned* bar = nullptr;         // grid-barrier counters and generation [kBarWords]
+    // brick-tiled passes (built lazily on the first step that needs them)
+    int pass_mapping = SRDR_PASS_AUTO;  // requested
+    int pass_tiled = -1;             // in use: -1 undecided, 0 sliced ELL, 1 bricks
+    int brick[3] = {0, 0, 0};        // requested brick size in cells (0: default)
+    int bricks_built = 0;            // 1 built, -1 does not fit
+    int nbricks = 0, max_halo = 0, max_own = 0, nbslices = 0;
+    int64_t bslots = 0;
+    srdr::BrickInfo* binfo = nullptr;  // [nbricks]
+    int* bown = nullptr;             // [n] sorted index of own particle k (brick order)
+    uint16_t* bown_h = nullptr;      // [n] its halo index
+    int* bhalo = nullptr;            // [sum of halos] sorted index of halo particle h
+    int* bsell_ptr = nullptr;        // [nbslices + 1] slot offsets of the brick slices
+    uint16_t* blidx = nullptr;       // [bslots] halo index of the neighbour in each slot
+    void* bg = nullptr;              // T [3][bslots] pair gradients
+    double* ke_pp = nullptr;         // [n] kinetic energy per particle (tiled pass B)
     int sweep_cells_per_warp = 2;    // cells per warp of the sweep kernel (1, 2, 4)
     int sweep_warps_per_block = 1;   // warps per block of the sweep kernel (1, 4)
     int sweep_tuned = 0;
@@ -211,15 +238,25 @@ inline double kernel_kc(int dim, double h)
 }
 
 // elements per particle of the AoS P B0 array (whole 16-byte vectors)
-inline int pb_stride(size_t tsize, int dim)
+// 16-byte chunks holding the dim x dim entries of one P B0 (FP32 3D: 3,
+// FP64 3D: 5, 2D: 1 or 2)
+__host__ __device__ constexpr int pb_chunks(size_t tsize, int dim)
 {
-    if (dim == 2) return 4;
-    return tsize == 4 ? 12 : 10;
+    return (int)((dim * dim * tsize + 15) / 16);
 }
+// T elements per particle in PB
+inline int pb_stride(size_t tsize, int dim) { return pb_chunks(tsize, dim) * (int)(16 / tsize); }
 
 // setup (setup.cu)
 srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* vol,
                        const uint8_t* flags, const double* u0);
+// brick layout of the tiled passes (setup.cu): builds it for the requested
+// brick size; b->bricks_built = 1 when built, -1 when a halo does not fit
+srdr_status build_bricks(srdr_body* b);
+// shared memory of the tiled passes per block for a halo of h particles
+inline size_t tile_smem_a(size_t tsize, int h) { (void)tsize; return (size_t)32 * h; }
+inline size_t tile_smem_b(size_t tsize, int dim, int h) { return 16 * (size_t)pb_chunks(tsize, dim) * h; }
+constexpr size_t kTileSmemMax = 200 * 1024;
 // kernel-class timing (api.cu): begin/end an interval of class k
 void prof_begin(srdr_body* b, int k, cudaEvent_t* ev);
 void prof_end(srdr_body* b, int k, cudaEvent_t ev);

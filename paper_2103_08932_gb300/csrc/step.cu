@@ -22,7 +22,7 @@ namespace srdr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;  // sliced-ELL slots per batch of loads in the passes
+constexpr int kUnroll = 8;  // sliced-ELL slots per batch of loads in the passes
 inline int nblocks(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
 #include "passes.cuh"
@@ -37,6 +37,7 @@ __device__ inline T warp_allsum(T x)
 }
 
 #include "sweep.cuh"
+#include "tiles.cuh"
 
 __global__ void k_set_tol(DevScalars* sc, double tol)
 {
@@ -182,6 +183,26 @@ srdr_status autotune_sweep(srdr_body* b)
     return dev_free(b, vtmp);
 }
 
+// Mapping of the stress and force passes: sliced ELL or brick tiles (see
+// srdr_body_pass_mapping).  The automatic choice is the sliced-ELL mapping,
+// the faster of the two on every body measured on GB300 (the brick layout is
+// then never built).
+template <typename T, int D, int MAT>
+srdr_status choose_pass_mapping(srdr_body* b)
+{
+    if (b->pass_mapping != SRDR_PASS_BRICKS) {
+        b->pass_tiled = 0;
+        return SRDR_OK;
+    }
+    if (b->bricks_built == 0) SRDR_TRY(build_bricks(b));
+    if (b->bricks_built < 0) {
+        set_error("a brick halo does not fit in shared memory: use smaller bricks or sliced ELL");
+        return SRDR_ERR_INVALID;
+    }
+    b->pass_tiled = 1;
+    return SRDR_OK;
+}
+
 template <typename T, int D, int MAT>
 srdr_status steps_typed(srdr_body* b, int64_t nsteps)
 {
@@ -204,6 +225,19 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         return SRDR_ERR_INVALID;
     }
     void* sweep_params[] = {&sw, &cptr, &ncol, &bar};
+    if (b->pass_tiled < 0) SRDR_TRY((choose_pass_mapping<T, D, MAT>(b)));
+    const bool tiled = b->pass_tiled == 1;
+    TileArgs<T> tl{};
+    size_t smem_a = 0, smem_b = 0;
+    if (tiled) {
+        tl = make_tile_args<T>(b);
+        smem_a = tile_smem_a(sizeof(T), b->max_halo);
+        smem_b = tile_smem_b(sizeof(T), D, b->max_halo);
+        SRDR_CK(cudaFuncSetAttribute((const void*)k_pass_a_tiled<T, D, MAT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+        SRDR_CK(cudaFuncSetAttribute((const void*)k_pass_b_tiled<T, D>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    }
     cudaEvent_t ev = nullptr;
     auto counted = [&](int k, int nlaunch) {
         b->k_launch[k] += nlaunch;
@@ -213,11 +247,17 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         const uint64_t step = (uint64_t)(b->step + s);
         const bool damp = damping && random_phi(b->desc.seed, step) < b->desc.alpha;
         prof_begin(b, SRDR_K_PASS_A, &ev);
-        k_pass_a<T, D, MAT><<<nb, kThreads, 0, st>>>(a);
+        if (tiled)
+            k_pass_a_tiled<T, D, MAT><<<b->nbricks, kTileThreads, smem_a, st>>>(a, tl);
+        else
+            k_pass_a<T, D, MAT><<<nb, kThreads, 0, st>>>(a);
         prof_end(b, SRDR_K_PASS_A, ev);
         counted(SRDR_K_PASS_A, 1);
         prof_begin(b, SRDR_K_PASS_B, &ev);
-        k_pass_b<T, D><<<nb, kThreads, 0, st>>>(a, damp ? 0 : 1);
+        if (tiled)
+            k_pass_b_tiled<T, D><<<b->nbricks, kTileThreads, smem_b, st>>>(a, tl, damp ? 0 : 1);
+        else
+            k_pass_b<T, D><<<nb, kThreads, 0, st>>>(a, damp ? 0 : 1);
         prof_end(b, SRDR_K_PASS_B, ev);
         counted(SRDR_K_PASS_B, 1);
         if (damp) {
@@ -233,9 +273,10 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
             counted(SRDR_K_FINISH, 1);
         }
         prof_begin(b, SRDR_K_KE, &ev);
+        if (tiled && !damp) k_ke_slices<<<nb, kThreads, 0, st>>>(b->ke_pp, (int)b->n, b->ke_part, b->sc);
         k_ke_final<<<1, kThreads, 0, st>>>(b->ke_part, b->nslices, b->sc, damp ? 1 : 0);
         prof_end(b, SRDR_K_KE, ev);
-        counted(SRDR_K_KE, 1);
+        counted(SRDR_K_KE, tiled && !damp ? 2 : 1);
     }
     SRDR_CK(cudaGetLastError());
     b->step += nsteps;

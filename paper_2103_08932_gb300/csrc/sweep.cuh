@@ -102,42 +102,56 @@ __device__ inline FootRuns foot_runs_group(int c, int dim, int nx, int ny, int n
 }
 
 // ---------------------------------------------------------------- grid barrier
-// Bounded grid barrier of a cooperative launch (all blocks co-resident).  The
-// last block to arrive resets the count and bumps the generation; the others
-// wait on the generation with a sleep, and give up after 2^24 polls, setting
-// DEV_TIMEOUT in sc->status so that the host gets an error instead of a hung
-// GPU.  Thread 0 of the block does the protocol; every thread of the block
-// must call it.
-__device__ inline bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks,
-                                    DevScalars* sc)
+// Bounded, split-phase grid barrier of a cooperative launch (all blocks
+// co-resident).  Words of the barrier buffer (kBarWords unsigned, zeroed at
+// creation), each group on its own 128-byte line:
+//   sub-counter k (k < kBarSub) at 32 k, top counter at 32 kBarSub,
+//   generation at 32 (kBarSub + 1).
+// Block b arrives at sub-counter b mod S (S = min(kBarSub, blocks)); the last
+// arrival of a sub-counter resets it and arrives at the top counter; the last
+// arrival there resets it and bumps the generation.  Waiters poll the
+// generation (its own line, so polling does not slow the counters) with a
+// sleep and give up after 2^24 polls, setting DEV_TIMEOUT in sc->status, so
+// the host gets an error instead of a hung GPU.  Between arrive and wait a
+// block may do work that does not depend on other blocks.
+__device__ inline unsigned bar_arrive(unsigned* bar, unsigned nblocks)
 {
-    __shared__ int s_ok;
-    __syncthreads();
-    int ok = 1;
-    if (threadIdx.x == 0) {
-        unsigned g = *gen;
+    volatile unsigned* gen = bar + 32 * (kBarSub + 1);
+    const unsigned g = *gen;
+    __threadfence();  // the block's writes (ordered by the block barrier) before the arrival
+    const unsigned ns = nblocks < (unsigned)kBarSub ? nblocks : (unsigned)kBarSub;
+    const unsigned k = blockIdx.x % ns;
+    const unsigned nk = nblocks / ns + (k < nblocks % ns ? 1u : 0u);
+    unsigned* sub = bar + 32 * k;
+    if (atomicAdd(sub, 1u) == nk - 1) {
+        atomicExch(sub, 0u);
         __threadfence();
-        if (atomicAdd(count, 1u) == nblocks - 1) {
-            atomicExch(count, 0u);
+        unsigned* top = bar + 32 * kBarSub;
+        if (atomicAdd(top, 1u) == ns - 1) {
+            atomicExch(top, 0u);
             __threadfence();
             atomicAdd(const_cast<unsigned*>(gen), 1u);
-        } else {
-            long long polls = 0;
-            while (*gen == g) {
-                if (++polls > (1LL << 24)) {
-                    atomicCAS(&sc->status, DEV_OK, DEV_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
         }
-        __threadfence();
-        if (*(volatile int*)&sc->status == DEV_TIMEOUT) ok = 0;
-        s_ok = ok;
     }
-    __syncthreads();
-    return s_ok != 0;
+    return g;
+}
+
+__device__ inline bool bar_wait(unsigned* bar, unsigned g, DevScalars* sc)
+{
+    volatile unsigned* gen = bar + 32 * (kBarSub + 1);
+    long long polls = 0;
+    bool ok = true;
+    while (*gen == g) {
+        if (++polls > (1LL << 24)) {
+            atomicCAS(&sc->status, DEV_OK, DEV_TIMEOUT);
+            ok = false;
+            break;
+        }
+        __nanosleep(100);
+    }
+    __threadfence();
+    if (*(volatile int*)&sc->status == DEV_TIMEOUT) ok = false;
+    return ok;
 }
 
 // ---------------------------------------------------------------- shared memory
@@ -390,7 +404,8 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
                     sv[j] = V4{o[0], o[1], o[2], x.w};
                 }
             }
-            __syncwarp(gmask);
+            // no lane writes record li above (rows exclude the particle
+            // itself) and every lane read it before the reduction's shuffles
             if (gl == 0) sv[li] = V4{vin[0], vin[1], vin[2], vi4.w};
             __syncwarp(gmask);
 #pragma unroll
@@ -490,25 +505,41 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
     const CellSmem<T, D> s = cell_smem<T, D>(smem_raw + (size_t)(wb * G + g) * cell_bytes, a.max_foot,
                                              a.max_pairs, a.max_cell);
     const int q0 = (blockIdx.x * W + wb) * G + g, qs = gridDim.x * W * G;
+    __shared__ unsigned s_gen;
+    __shared__ int s_ok;
     // the group's first cell, staged before the first phase
     int staged = first_item(colour_ptr, ncolours, 0, q0);
     CellStage st{};
     if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
     int phases = 0;
+    bool restage = false;  // staging of the next item waits for the barrier's arrive
     for (int ph = 0; ph < 2 * ncolours; ++ph) {
         const int backward = ph >= ncolours;
         const int col = backward ? 2 * ncolours - 1 - ph : ph;
         const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
         if (c1 == c0) continue;
-        if (phases++ > 0 && !grid_barrier(bar, bar + 1, gridDim.x, a.sc)) {
-            cp_async_wait_all();  // no copy may land after the block has left
-            return;
+        if (phases++ > 0) {
+            // arrive, stage the next cell while the other blocks finish, wait
+            __syncthreads();
+            if (threadIdx.x == 0) s_gen = bar_arrive(bar, gridDim.x);
+            if (restage && staged >= 0)
+                st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
+            restage = false;
+            if (threadIdx.x == 0) s_ok = bar_wait(bar, s_gen, a.sc) ? 1 : 0;
+            __syncthreads();
+            if (!s_ok) {
+                cp_async_wait_all();  // no copy may land after the block has left
+                return;
+            }
         }
         for (int cid = c0 + q0; cid < c1; cid += qs) {
             // staged == cid here: items are visited in the order next_item gives
             run_cell<T, D, L>(a, st, backward, s, gl, gmask);
             staged = next_item(colour_ptr, ncolours, ph, cid, q0, qs);
-            if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
+            if (staged >= 0 && staged < c1 && staged >= c0)
+                st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
+            else
+                restage = true;  // a later phase: staged between arrive and wait
         }
         __syncwarp();
     }

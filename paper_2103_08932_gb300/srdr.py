@@ -17,6 +17,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsrdr.so")
 
+SRDR_PASS_AUTO = 0
+SRDR_PASS_SELL = 1
+SRDR_PASS_BRICKS = 2
 SRDR_OK = 0
 SRDR_ERR_INVALID = -1
 SRDR_ERR_NO_MEMORY = -2
@@ -42,6 +45,7 @@ EXPORTS = [
     "srdr_body_read_field", "srdr_body_destroy", "srdr_last_error", "srdr_philox4x64_10",
     "srdr_random_phi", "srdr_body_profile", "srdr_body_kernel_times",
     "srdr_kinetic_energy_noalloc", "srdr_body_tune", "srdr_desc_particle_count",
+    "srdr_body_pass_mapping",
     "srdr_batch_create", "srdr_batch_step", "srdr_batch_run", "srdr_batch_info",
     "srdr_batch_destroy", "srdr_batch_relax", "srdr_server_create", "srdr_server_configure",
     "srdr_server_submit", "srdr_server_poll", "srdr_server_wait", "srdr_server_stats",
@@ -83,7 +87,7 @@ class srdr_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("damped_steps", C.c_int64), ("ke", C.c_double),
                 ("ke_max", C.c_double), ("eta", C.c_double), ("dt", C.c_double),
                 ("converged", C.c_int), ("launches", C.c_int64),
-                ("sweep_cells_per_warp", C.c_int)]
+                ("sweep_cells_per_warp", C.c_int), ("pass_mapping", C.c_int)]
 
 
 class srdr_kernel_times(C.Structure):
@@ -126,6 +130,7 @@ def lib():
         "srdr_body_profile": (st, [p, C.c_int]),
         "srdr_body_kernel_times": (st, [p, C.POINTER(srdr_kernel_times)]),
         "srdr_body_tune": (st, [p, C.c_int, C.c_int]),
+        "srdr_body_pass_mapping": (st, [p, C.c_int, C.c_int, C.c_int, C.c_int]),
         "srdr_desc_particle_count": (st, [C.POINTER(srdr_body_desc), C.POINTER(i64)]),
         "srdr_batch_create": (st, [p, C.c_int, p, C.POINTER(p)]),
         "srdr_batch_step": (st, [p, i64]),
@@ -265,6 +270,12 @@ class Body:
 
     def tune(self, sweep_cells_per_warp=0, sweep_warps_per_block=0):
         _check(lib().srdr_body_tune(self.h, int(sweep_cells_per_warp), int(sweep_warps_per_block)))
+
+    def pass_mapping(self, mapping=0, brick=(0, 0, 0)):
+        """SRDR_PASS_AUTO (0), SRDR_PASS_SELL (1) or SRDR_PASS_BRICKS (2),
+        with the brick size in cells (0 = default)."""
+        bx, by, bz = (int(x) for x in brick)
+        _check(lib().srdr_body_pass_mapping(self.h, int(mapping), bx, by, bz))
 
     def profile(self, enable=True):
         _check(lib().srdr_body_profile(self.h, 1 if enable else 0))

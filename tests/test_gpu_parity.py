@@ -294,3 +294,62 @@ def test_sweep_mapping_does_not_change_results(precision):
             assert b.stats()["sweep_cells_per_warp"] in (1, 2, 4)
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+JIT3D = S.BodySpec(dim=3, extent=(0.013, 0.005, 0.007), dp=1e-3, clamp_axis=0, clamp_layers=2,
+                   material=S.NEO_HOOKEAN, gravity=(0.0, -9.81, 3.0), beta=0.2, L_char=0.005,
+                   alpha=0.5, seed=1)
+
+
+@pytest.mark.parametrize("spec,precision,jit", [
+    (SMALL3D, srdr.SRDR_FP64, False), (SMALL3D, srdr.SRDR_FP32_MIXED, False),
+    (SMALL2D, srdr.SRDR_FP64, False), (SMALL2D, srdr.SRDR_FP32_MIXED, False),
+    (JIT3D, srdr.SRDR_FP32_MIXED, True), (JIT3D, srdr.SRDR_FP64, True)])
+def test_pass_mappings_are_bitwise_equal(spec, precision, jit):
+    """Sliced-ELL and brick-tiled stress/force passes (several brick sizes,
+    bricks cut by the body's edges, particles per brick not a multiple of 32)
+    visit each row in the same order with the same roundings: displacements,
+    velocities and kinetic energies agree bit for bit, on damped and undamped
+    steps."""
+    parts = S.jittered(spec, 0.3, 5) if jit else None
+    ref = gpu_for(spec, precision=precision, particles=parts)
+    ref.pass_mapping(srdr.SRDR_PASS_SELL)
+    ref.step(14)
+    assert ref.stats()["pass_mapping"] == srdr.SRDR_PASS_SELL
+    assert 0 < ref.stats()["damped_steps"] < 14
+    bricks = [(0, 0, 0), (1, 1, 1), (3, 2, 1), (4, 4, 4)]
+    for brick in bricks:
+        b = gpu_for(spec, precision=precision, particles=parts)
+        b.pass_mapping(srdr.SRDR_PASS_BRICKS, brick)
+        b.step(14)
+        st = b.stats()
+        assert st["pass_mapping"] == srdr.SRDR_PASS_BRICKS
+        assert np.array_equal(b.displacement(), ref.displacement()), brick
+        assert np.array_equal(b.velocity(), ref.velocity()), brick
+        assert st["ke"] == ref.stats()["ke"] and st["ke_max"] == ref.stats()["ke_max"], brick
+    auto = gpu_for(spec, precision=precision, particles=parts)
+    auto.step(14)
+    assert auto.stats()["pass_mapping"] in (srdr.SRDR_PASS_SELL, srdr.SRDR_PASS_BRICKS)
+    assert np.array_equal(auto.velocity(), ref.velocity())
+
+
+def test_brick_mapping_matches_oracle_fp64():
+    """The brick-tiled passes against the oracle directly (cantilever 2D, 30
+    steps, FP64), besides their bitwise equality with the sliced-ELL passes."""
+    spec = S.cantilever_2d(S.NEO_HOOKEAN)
+    ob = oracle_for(spec)
+    gb = gpu_for(spec)
+    gb.pass_mapping(srdr.SRDR_PASS_BRICKS, (2, 2, 1))
+    ob.step(30)
+    gb.step(30)
+    assert ob.damped_steps > 0
+    assert rel(gb.velocity(), ob.v) < 1e-9
+    assert rel(gb.displacement(), ob.u) < 1e-9
+
+
+def test_pass_mapping_rejects_bad_arguments():
+    b = gpu_for(SMALL3D)
+    for args in ((3, (0, 0, 0)), (-1, (0, 0, 0)), (2, (5, 1, 1)), (2, (1, -1, 1))):
+        with pytest.raises(srdr.SrdrError) as e:
+            b.pass_mapping(*args)
+        assert e.value.status == srdr.SRDR_ERR_INVALID
