@@ -126,11 +126,12 @@ __global__ void __launch_bounds__(kThreads) k_batch_ke(const BatchEntry<T>* __re
 // the start of phase ph) that belongs to a damped body, and its phase; -1
 // when there is none.  Group q0 takes items q0, q0 + qs, ... of each colour.
 __device__ inline int batch_next(const int2* __restrict__ cells, const int* __restrict__ damp,
-                                 const int* __restrict__ colour_ptr, int ncolours, int ph, int k, int q0,
-                                 int qs, int* item_ph)
+                                 const int* __restrict__ colour_ptr, int ncolours, int clast, int ph, int k,
+                                 int q0, int qs, int* item_ph)
 {
     for (int p = ph; p < 2 * ncolours; ++p) {
-        const int col = p >= ncolours ? 2 * ncolours - 1 - p : p;
+        const int col = phase_colour(p, ncolours);
+        if (p >= ncolours && col == clast) continue;  // fused into the forward phase
         const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
         for (int kk = (p == ph && k >= 0) ? k + qs : c0 + q0; kk < c1; kk += qs)
             if (damp[cells[kk].x]) {
@@ -142,7 +143,8 @@ __device__ inline int batch_next(const int2* __restrict__ cells, const int* __re
 }
 
 // S_d of every damped body: colour c of all bodies, then c+1, ...; forward
-// then backward; group g of block bb takes work items bb*G+g, +gridDim*G, ...
+// then backward (the last colour's two phases fused); group g of block bb
+// takes work items bb*G+g, +gridDim*G, ...
 // As in the single-body sweep, the read-only data of a group's next item is
 // staged between the barrier's arrive and wait.
 template <typename T, int D, int G>
@@ -164,7 +166,8 @@ __global__ void __launch_bounds__(32) k_batch_sweep(const BatchEntry<T>* __restr
         cell_smem<T, D>(smem_raw + (size_t)g * cell_smem_bytes<T, D>(F, P, C), F, P, C);
     const int q0 = blockIdx.x * G + g, qs = gridDim.x * G;
     int sph = 0;
-    int staged = batch_next(cells, damp, colour_ptr, ncolours, 0, -1, q0, qs, &sph);
+    const int clast = last_colour(colour_ptr, ncolours);
+    int staged = batch_next(cells, damp, colour_ptr, ncolours, clast, 0, -1, q0, qs, &sph);
     CellStage st{};
     if (staged >= 0) {
         const int2 e = cells[staged];
@@ -176,7 +179,8 @@ __global__ void __launch_bounds__(32) k_batch_sweep(const BatchEntry<T>* __restr
         const int backward = ph >= ncolours;
         const int col = backward ? 2 * ncolours - 1 - ph : ph;
         const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
-        if (c1 == c0) continue;
+        if (c1 == c0 || (backward && col == clast)) continue;
+        const int mode = col == clast ? 2 : backward;
         if (phases++ > 0) {
             __syncthreads();
             if (threadIdx.x == 0) s_gen = bar_arrive(bar, gridDim.x);
@@ -194,8 +198,8 @@ __global__ void __launch_bounds__(32) k_batch_sweep(const BatchEntry<T>* __restr
         }
         while (staged >= 0 && sph == ph) {
             const int2 e = cells[staged];
-            run_cell<T, D, L>(tab[e.x].sweep, st, backward, s, gl, gmask);
-            staged = batch_next(cells, damp, colour_ptr, ncolours, ph, staged, q0, qs, &sph);
+            run_cell<T, D, L>(tab[e.x].sweep, st, mode, s, gl, gmask);
+            staged = batch_next(cells, damp, colour_ptr, ncolours, clast, ph, staged, q0, qs, &sph);
             if (staged >= 0 && sph == ph) {
                 const int2 e2 = cells[staged];
                 st = stage_cell<T, D, L>(tab[e2.x].sweep, e2.y, s, gl, gmask);
@@ -311,8 +315,8 @@ SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
     s.mass = static_cast<const T*>(b->mass);
-    s.sumw = static_cast<const T*>(b->sumw);
-    s.sumw2 = static_cast<const T*>(b->sumw2);
+    s.sbm = static_cast<const T*>(b->sbm);
+    s.srd = static_cast<const T*>(b->srd);
     s.v = static_cast<T*>(b->v);
     s.sc = b->sc;
     s.c = b->desc.alpha > 0 ? (T)(b->eta / b->desc.alpha * b->dt) : T(0);
@@ -331,6 +335,8 @@ srdr_status upload_table(srdr_batch* bt)
     for (int k = 0; k < nb; ++k) {
         srdr_body* b = bt->bodies[k];
         tab[k].step = make_step_args<T>(b);
+        if (b->desc.damping != SRDR_DAMP_NONE && b->desc.alpha > 0.0 && b->eta > 0.0 && !b->sbm)
+            SRDR_TRY(prepare_sweep(b));
         tab[k].sweep = sweep_args<T>(b, bt->F, bt->P, bt->C);
         tab[k].material = b->desc.material;
         tab[k].damping_on = b->desc.damping != SRDR_DAMP_NONE && b->desc.alpha > 0 && b->eta > 0;

@@ -1051,6 +1051,49 @@ srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* 
     return build_typed<float>(b, n, r0, vol, flags, u0);
 }
 
+template <typename T>
+__global__ void k_sweep_consts(int n, T c, const T* __restrict__ mass, const T* __restrict__ sumw,
+                               const T* __restrict__ sumw2, T* __restrict__ sbm, T* __restrict__ srd)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if constexpr (sizeof(T) == 4) {
+        const float sb = __fmul_rn(c, sumw[i]), sb2 = __fmul_rn(__fmul_rn(c, c), sumw2[i]);
+        const float d = __fsub_rn(sb, mass[i]);
+        sbm[i] = d;
+        srd[i] = __fdiv_rn(1.0f, __fmaf_rn(d, d, sb2));
+    } else {
+        const double sb = __dmul_rn(c, sumw[i]), sb2 = __dmul_rn(__dmul_rn(c, c), sumw2[i]);
+        const double d = __dsub_rn(sb, mass[i]);
+        sbm[i] = d;
+        srd[i] = __ddiv_rn(1.0, __fma_rn(d, d, sb2));
+    }
+}
+
+template <typename T>
+srdr_status prepare_sweep_typed(srdr_body* b)
+{
+    if (!b->sbm) {
+        T *x = nullptr, *y = nullptr;
+        SRDR_TRY(dalloc(b, &x, b->n));
+        SRDR_TRY(dalloc(b, &y, b->n));
+        b->sbm = x;
+        b->srd = y;
+    }
+    const T c = (T)(b->eta / b->desc.alpha * b->dt);
+    k_sweep_consts<T><<<nblocks(b->n), kThreads, 0, b->stream>>>(
+        (int)b->n, c, static_cast<const T*>(b->mass), static_cast<const T*>(b->sumw),
+        static_cast<const T*>(b->sumw2), static_cast<T*>(b->sbm), static_cast<T*>(b->srd));
+    SRDR_CK(cudaGetLastError());
+    return SRDR_OK;
+}
+
+srdr_status prepare_sweep(srdr_body* b)
+{
+    if (b->prec == SRDR_FP64) return prepare_sweep_typed<double>(b);
+    return prepare_sweep_typed<float>(b);
+}
+
 srdr_status build_bricks(srdr_body* b)
 {
     for (int a = 0; a < 3; ++a)

@@ -117,8 +117,8 @@ struct SweepArgs {
     const uint16_t* __restrict__ loc;
     const T* __restrict__ w;
     const T* __restrict__ mass;
-    const T* __restrict__ sumw;
-    const T* __restrict__ sumw2;
+    const T* __restrict__ sbm;   // [n] sum_j B_j - m_i of the local solve (Sec. 3.1)
+    const T* __restrict__ srd;   // [n] 1 / ((sum_j B_j - m_i)^2 + sum_j B_j^2)
     T* __restrict__ v;
     DevScalars* sc;
     T c;          // 2 eta~ dt_loc, so that B_j = c w_ij
@@ -170,6 +170,8 @@ struct srdr_body {
     void* Gs = nullptr;         // T [3][n]
     void* sumw = nullptr;
     void* sumw2 = nullptr;
+    void* sbm = nullptr;         // T [n] per-particle constants of the local solve
+    void* srd = nullptr;         //   (prepare_sweep; B_j = c w_ij with the body's c)
     void* v = nullptr;          // T [n][4] (vx, vy, vz, 1/m)
     double* u = nullptr;        // FP64 [3][n]
     float* uhi = nullptr;       // [n][4] FP32 mode
@@ -250,6 +252,10 @@ inline int pb_stride(size_t tsize, int dim) { return pb_chunks(tsize, dim) * (in
 // setup (setup.cu)
 srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* vol,
                        const uint8_t* flags, const double* u0);
+// per-particle constants of the damping sweep's local solve for the body's
+// current eta~ and dt (setup.cu): sbm = c sum_j w_ij - m_i and
+// srd = 1 / (sbm^2 + c^2 sum_j w_ij^2) with c = 2 eta~ dt_loc
+srdr_status prepare_sweep(srdr_body* b);
 // brick layout of the tiled passes (setup.cu): builds it for the requested
 // brick size; b->bricks_built = 1 when built, -1 when a halo does not fit
 srdr_status build_bricks(srdr_body* b);

@@ -63,8 +63,8 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
     s.mass = static_cast<const T*>(b->mass);
-    s.sumw = static_cast<const T*>(b->sumw);
-    s.sumw2 = static_cast<const T*>(b->sumw2);
+    s.sbm = static_cast<const T*>(b->sbm);
+    s.srd = static_cast<const T*>(b->srd);
     s.v = static_cast<T*>(b->v);
     s.sc = b->sc;
     // B_j = 2 eta~ V_i V_j W'/r dt_loc with eta~ = eta / alpha, dt_loc = dt / 2
@@ -208,9 +208,10 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
 {
     cudaStream_t st = b->stream;
     StepArgs<T> a = make_step_args<T>(b);
-    SweepArgs<T> sw = make_sweep_args<T>(b);
     const int nb = nblocks(b->n);
     const bool damping = b->desc.damping != SRDR_DAMP_NONE && b->desc.alpha > 0.0 && b->eta > 0.0;
+    if (damping && !b->sbm) SRDR_TRY(prepare_sweep(b));
+    SweepArgs<T> sw = make_sweep_args<T>(b);
     SweepLaunch<T, D> sl;
     if (damping && !b->sweep_tuned) SRDR_TRY((autotune_sweep<T, D>(b)));
     if (damping) SRDR_TRY((sweep_launch<T, D>(b, &sl)));
@@ -220,7 +221,7 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
     int ncol = b->ncolours;
     unsigned* bar = b->bar;
     if (damping && (!sw.colour_cells || !sw.cell_start || !sw.row_ptr || !sw.loc || !sw.w ||
-                    !sw.mass || !sw.sumw || !sw.sumw2 || !sw.v || !cptr || !bar)) {
+                    !sw.mass || !sw.sbm || !sw.srd || !sw.v || !cptr || !bar)) {
         set_error("damping sweep tables are not built");
         return SRDR_ERR_INVALID;
     }

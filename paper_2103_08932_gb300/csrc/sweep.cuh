@@ -156,9 +156,10 @@ __device__ inline bool bar_wait(unsigned* bar, unsigned g, DevScalars* sc)
 
 // ---------------------------------------------------------------- shared memory
 // Per cell (group):
-//   sv [F] footprint velocity records (vx, vy, vz, 1/m), sw [P] weights,
-//   sm / sbm / srd [C] per particle of the cell: mass, then (after staging)
-//   sum_B - m_i and 1 / ((sum_B - m_i)^2 + sum_B^2) (loaded as sum w, sum w^2),
+//   sv [F + 1] footprint velocity records (vx, vy, vz, 1/m) and a zero
+//   record at F that padded neighbour slots point at, sw [P] weights,
+//   sm / sbm / srd [C] per particle of the cell: mass, sum_B - m_i and
+//   1 / ((sum_B - m_i)^2 + sum_B^2) (precomputed per body),
 //   srow [C+1] absolute row starts, sl [P+4] footprint-local indices (uint16)
 template <typename T, int D>
 struct CellSmem {
@@ -174,7 +175,7 @@ struct CellSmem {
 template <typename T, int D>
 __host__ __device__ inline size_t cell_smem_bytes(int F, int P, int C)
 {
-    size_t b = sizeof(T) * (4 * (size_t)F + (size_t)P + 3 * (size_t)C);
+    size_t b = sizeof(T) * (4 * ((size_t)F + 1) + (size_t)P + 3 * (size_t)C);
     b = (b + 3) & ~size_t(3);
     b += sizeof(int) * ((size_t)C + 1);
     b += sizeof(uint16_t) * ((size_t)P + 4);
@@ -186,11 +187,11 @@ __device__ inline CellSmem<T, D> cell_smem(unsigned char* raw, int F, int P, int
 {
     CellSmem<T, D> s;
     s.sv = reinterpret_cast<vec4_t<T>*>(raw);
-    s.sw = reinterpret_cast<T*>(raw) + 4 * (size_t)F;
+    s.sw = reinterpret_cast<T*>(raw) + 4 * ((size_t)F + 1);
     s.sm = s.sw + P;
     s.sbm = s.sm + C;
     s.srd = s.sbm + C;
-    size_t off = sizeof(T) * (4 * (size_t)F + (size_t)P + 3 * (size_t)C);
+    size_t off = sizeof(T) * (4 * ((size_t)F + 1) + (size_t)P + 3 * (size_t)C);
     off = (off + 3) & ~size_t(3);
     s.srow = reinterpret_cast<int*>(raw + off);
     s.sl = reinterpret_cast<uint16_t*>(s.srow + C + 1);
@@ -243,17 +244,19 @@ __device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellS
     for (int p = gl; p <= np; p += L) cp_async4(s.srow + p, a.row_ptr + st.cs + p);
     for (int p = gl; p < np; p += L) {
         cp_async_t(s.sm + p, a.mass + st.cs + p);
-        cp_async_t(s.sbm + p, a.sumw + st.cs + p);
-        cp_async_t(s.srd + p, a.sumw2 + st.cs + p);
+        cp_async_t(s.sbm + p, a.sbm + st.cs + p);
+        cp_async_t(s.srd + p, a.srd + st.cs + p);
     }
     return st;
 }
 
 // Sweep the staged cell: fetch the footprint's velocity records, then the
-// local operators of its particles in order (backward: reverse order), then
-// write the footprint back.
+// local operators of its particles in order (mode 0), in reverse order
+// (mode 1) or in order and then in reverse order (mode 2: the last colour's
+// forward and backward phases, fused since its cells' footprints are
+// disjoint), then write the footprint back.
 template <typename T, int D, int L>
-__device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int backward,
+__device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int mode,
                                 const CellSmem<T, D>& s, int gl, unsigned gmask)
 {
     using V4 = vec4_t<T>;
@@ -279,20 +282,14 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
             if (q < Ftot) sv[q] = tv[u];
         }
     }
+    if (gl == 0) sv[a.max_foot] = V4{T(0), T(0), T(0), T(0)};
     cp_async_wait_all();
     __syncwarp(gmask);
-    // per particle of the cell: sum_B - m_i and the local solve's denominator
-    for (int p = gl; p < np; p += L) {
-        const T mi = s.sm[p];
-        const T SB = cc * s.sbm[p];
-        const T SB2 = cc * cc * s.srd[p];
-        const T sbm = SB - mi;
-        s.sbm[p] = sbm;
-        s.srd[p] = T(1) / (sbm * sbm + SB2);
-    }
-    __syncwarp(gmask);
     const uint16_t* sl = s.sl + (p0 & 1);  // entry k at sl[k - p0]
+    const int pad = a.max_foot;  // the zero record: padded slots read and write it with B = 0
 
+    for (int dir = mode == 1 ? 1 : 0; dir <= (mode == 0 ? 0 : 1); ++dir) {
+    const int backward = dir;
     if (!a.pairwise) {
         // E_i = -sum_j B_j (v_i - v_j), summed in the order of a 32-lane
         // butterfly whatever L is: lane gl of the group keeps the 32/L
@@ -314,7 +311,7 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
             for (int m = 0; m < NK; ++m) {
                 const int k = a0 + gl + m * L;
                 const bool ok = k < a1;
-                j_[m] = ok ? (int)sl[k] : my_off + p;
+                j_[m] = ok ? (int)sl[k] : pad;
                 b_[m] = ok ? cc * sw[k] : T(0);
             }
         };
@@ -382,16 +379,16 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
             }
             // v_j <- v_j - B_j (v_i^new - v_j^p) / m_j,  v_j^p = v_j - B_j k
             if (in_regs) {
+                // padded slots write the zero record back unchanged (B = 0)
 #pragma unroll
-                for (int m = 0; m < NK; ++m)
-                    if (k0 + gl + m * L < k1) {
-                        const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
-                        T o[3] = {vjd[0], vjd[1], vjd[2]};
+                for (int m = 0; m < NK; ++m) {
+                    const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
+                    T o[3] = {vjd[0], vjd[1], vjd[2]};
 #pragma unroll
-                        for (int d = 0; d < D; ++d)
-                            o[d] = vjd[d] - BB[m] * (vin[d] - vjd[d] + BB[m] * kk[d]) * vj[m].w;
-                        sv[jj[m]] = V4{o[0], o[1], o[2], vj[m].w};
-                    }
+                    for (int d = 0; d < D; ++d)
+                        o[d] = vjd[d] - BB[m] * (vin[d] - vjd[d] + BB[m] * kk[d]) * vj[m].w;
+                    sv[jj[m]] = V4{o[0], o[1], o[2], vj[m].w};
+                }
             } else {
                 for (int k = k0 + gl; k < k1; k += L) {
                     const int j = sl[k];
@@ -450,6 +447,7 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
         }
         __syncwarp(gmask);
     }
+    }  // dir
     // write the footprint back (through L2: other SMs read it after the barrier)
     for (int q = gl; q < Ftot; q += L) stcg_v4<T>(a.v, st.fr.particle(q), sv[q]);
     __syncwarp(gmask);
@@ -457,19 +455,34 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
 
 // Both stages back to back.
 template <typename T, int D, int L>
-__device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int backward, const CellSmem<T, D>& s,
+__device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int mode, const CellSmem<T, D>& s,
                                   int gl, unsigned gmask)
 {
     const CellStage st = stage_cell<T, D, L>(a, c, s, gl, gmask);
-    run_cell<T, D, L>(a, st, backward, s, gl, gmask);
+    run_cell<T, D, L>(a, st, mode, s, gl, gmask);
+}
+
+// Colour of phase ph (forward colours 0..nc-1, then backward nc-1..0).
+__device__ inline int phase_colour(int ph, int ncolours) { return ph >= ncolours ? 2 * ncolours - 1 - ph : ph; }
+
+// The last colour with cells: its backward phase is fused into its forward
+// phase (mode 2 of run_cell) and skipped.
+__device__ inline int last_colour(const int* __restrict__ colour_ptr, int ncolours)
+{
+    int c = -1;
+    for (int k = 0; k < ncolours; ++k)
+        if (__ldg(colour_ptr + k + 1) > __ldg(colour_ptr + k)) c = k;
+    return c;
 }
 
 // The first item of group q0 at or after phase ph (its first cell of that
-// phase), or -1 when there is none.
-__device__ inline int first_item(const int* __restrict__ colour_ptr, int ncolours, int ph, int q0)
+// phase), or -1 when there is none; the fused backward phase of colour
+// clast is skipped.
+__device__ inline int first_item(const int* __restrict__ colour_ptr, int ncolours, int clast, int ph, int q0)
 {
     for (int p = ph; p < 2 * ncolours; ++p) {
-        const int c = p >= ncolours ? 2 * ncolours - 1 - p : p;
+        const int c = phase_colour(p, ncolours);
+        if (p >= ncolours && c == clast) continue;
         const int c0 = __ldg(colour_ptr + c), c1 = __ldg(colour_ptr + c + 1);
         if (c0 + q0 < c1) return c0 + q0;
     }
@@ -478,17 +491,17 @@ __device__ inline int first_item(const int* __restrict__ colour_ptr, int ncolour
 
 // The item a group takes after item cid of phase ph: the next of the same
 // phase (stride qs), else its first of a later phase.
-__device__ inline int next_item(const int* __restrict__ colour_ptr, int ncolours, int ph, int cid, int q0,
-                                int qs)
+__device__ inline int next_item(const int* __restrict__ colour_ptr, int ncolours, int clast, int ph, int cid,
+                                int q0, int qs)
 {
-    const int col = ph >= ncolours ? 2 * ncolours - 1 - ph : ph;
+    const int col = phase_colour(ph, ncolours);
     if (cid + qs < __ldg(colour_ptr + col + 1)) return cid + qs;
-    return first_item(colour_ptr, ncolours, ph + 1, q0);
+    return first_item(colour_ptr, ncolours, clast, ph + 1, q0);
 }
 
 // The whole S_d of one damped step in one cooperative launch: colours
 // 0..3^d-1 forward, then 3^d-1..0 backward, a bounded grid barrier between
-// colour phases.  Blocks of W warps, G cell groups per warp; group number
+// colour phases; the last colour runs both directions in one phase.  Blocks of W warps, G cell groups per warp; group number
 // q = (block * W + warp) * G + g takes the colour's cells q, q + gridDim*W*G, ...
 // More warps per block means fewer blocks arriving at the grid barrier.
 template <typename T, int D, int G, int W>
@@ -507,8 +520,9 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
     const int q0 = (blockIdx.x * W + wb) * G + g, qs = gridDim.x * W * G;
     __shared__ unsigned s_gen;
     __shared__ int s_ok;
+    const int clast = last_colour(colour_ptr, ncolours);
     // the group's first cell, staged before the first phase
-    int staged = first_item(colour_ptr, ncolours, 0, q0);
+    int staged = first_item(colour_ptr, ncolours, clast, 0, q0);
     CellStage st{};
     if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
     int phases = 0;
@@ -517,7 +531,8 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
         const int backward = ph >= ncolours;
         const int col = backward ? 2 * ncolours - 1 - ph : ph;
         const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
-        if (c1 == c0) continue;
+        if (c1 == c0 || (backward && col == clast)) continue;
+        const int mode = col == clast ? 2 : backward;
         if (phases++ > 0) {
             // arrive, stage the next cell while the other blocks finish, wait
             __syncthreads();
@@ -534,8 +549,8 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
         }
         for (int cid = c0 + q0; cid < c1; cid += qs) {
             // staged == cid here: items are visited in the order next_item gives
-            run_cell<T, D, L>(a, st, backward, s, gl, gmask);
-            staged = next_item(colour_ptr, ncolours, ph, cid, q0, qs);
+            run_cell<T, D, L>(a, st, mode, s, gl, gmask);
+            staged = next_item(colour_ptr, ncolours, clast, ph, cid, q0, qs);
             if (staged >= 0 && staged < c1 && staged >= c0)
                 st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
             else
