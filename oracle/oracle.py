@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "srdr_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libsrdr_oracle.so")
 
 SVK, NEO_HOOKEAN = 0, 1
-DAMP_NONE, DAMP_PARTICLE, DAMP_PAIRWISE = 0, 1, 2
+DAMP_NONE, DAMP_PARTICLE, DAMP_PAIRWISE, DAMP_EXPLICIT = 0, 1, 2, 3
 F_RATE, F_DISPLACEMENT = 0, 1
 FLAG_CONSTRAINED, FLAG_END_LOAD = 1, 2
 U, V, F, PB, B0, ACC = 0, 1, 2, 3, 4, 5
@@ -101,6 +101,7 @@ def lib():
         L.ora_body_Fdot.argtypes = [p, p, p]
         L.ora_body_acc.argtypes = [p, p, p]
         L.ora_body_damp.argtypes = [p, d, d]
+        L.ora_body_viscous_acc.argtypes = [p, d, p, p]
         L.ora_body_local_update.argtypes = [p, i64, d, d, p]
     return _lib
 
@@ -336,6 +337,13 @@ class OracleBody:
         Fa = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(self.n, 9))
         out = np.zeros((self.n, 3))
         lib().ora_body_acc(self._h, _ptr(Fa), _ptr(out))
+        return out
+
+    def viscous_acc(self, eta, v):
+        """Eq. damping-term for the velocity field v (explicit comparator)."""
+        va = _vec3(v, self.dim)
+        out = np.zeros((self.n, 3))
+        lib().ora_body_viscous_acc(self._h, eta, _ptr(va), _ptr(out))
         return out
 
     def damp(self, eta_tilde, dt_loc):

@@ -33,6 +33,11 @@
  *   R12 dt fixed per body: Eq. time-step-criterion with |v|max = 0 and
  *       |a|max = the largest body-force magnitude, min'd with the implicit
  *       viscous limit 50 h^2 / (nu~ D), nu~ = eta / (alpha rho0).
+ *   R16 Explicit-viscosity comparator (ORA_DAMP_EXPLICIT, Sec. 3): the term of
+ *       Eq. damping-term with eta itself (no random choice) is evaluated at
+ *       v^n and added to the acceleration of S_m; dt is min'd with the
+ *       explicit limit 0.5 h^2 / (nu D), nu = eta / rho0 (Eq.
+ *       viscous-criteria-o).
  */
 #include "srdr_oracle.h"
 
@@ -533,7 +538,13 @@ static double body_dt(const ora_body* b)
         if (t < dt) dt = t;
     }
     dt *= 0.6;
-    if (p->damping != ORA_DAMP_NONE && p->alpha > 0.0 && b->eta > 0.0) {
+    if (p->damping == ORA_DAMP_EXPLICIT) {
+        if (b->eta > 0.0) {
+            double nu = b->eta / p->rho0;
+            double tv = 0.5 * p->h * p->h / (nu * (double)dim); /* Eq. viscous-criteria-o */
+            if (tv < dt) dt = tv;
+        }
+    } else if (p->damping != ORA_DAMP_NONE && p->alpha > 0.0 && b->eta > 0.0) {
         double nu_t = b->eta / (p->alpha * p->rho0);
         double tv = 50.0 * p->h * p->h / (nu_t * (double)dim); /* Eq. viscous-criteria */
         if (tv < dt) dt = tv;
@@ -749,6 +760,23 @@ static double coeff_B(const ora_body* b, int64_t i, int64_t k, double eta, doubl
     return 2.0 * eta * b->vol[i] * b->vol[j] * (1.0 / b->rij[k]) * b->dW[k] * dt;
 }
 
+/* Eq. damping-term: a_i = (2 eta / m_i) sum_j V_i V_j v_ij / r_ij (dW/dr)_ij */
+void ora_body_viscous_acc(const ora_body* b, double eta, const double* v, double* out)
+{
+    int dim = b->p.dim;
+    for (int64_t i = 0; i < b->n; ++i) {
+        double a[3] = {0, 0, 0};
+        double Vi = b->mass[i] / b->p.rho0;
+        for (int64_t k = b->row_ptr[i]; k < b->row_ptr[i + 1]; ++k) {
+            int64_t j = b->col[k];
+            double Vj = b->mass[j] / b->p.rho0;
+            double f = Vi * Vj * b->dW[k] / b->rij[k];
+            for (int c = 0; c < dim; ++c) a[c] += f * (v[i * 3 + c] - v[j * 3 + c]);
+        }
+        for (int c = 0; c < 3; ++c) out[i * 3 + c] = c < dim ? 2.0 * eta / b->mass[i] * a[c] : 0.0;
+    }
+}
+
 /* Sec. 3.1, particle-by-particle scheme: Eqs. parameters1, parameters2,
  * learning-rate-solve, first-step and second-step. */
 static void local_update_particle(const ora_body* b, int64_t i, double eta, double dt, double* v)
@@ -870,14 +898,23 @@ static void one_step(ora_body* b)
         ora_body_F_from_u(b, uh, Fh);
     }
 
-    /* S_m: v^* = v^n + dt dv/dt, dv/dt from the stress at F^{n+1/2} */
+    /* S_m: v^* = v^n + dt dv/dt, dv/dt from the stress at F^{n+1/2}; the
+     * explicit comparator adds the viscous term at v^n (reading R16) */
     ora_body_acc(b, Fh, b->acc);
+    if (b->p.damping == ORA_DAMP_EXPLICIT && b->eta > 0.0) {
+        double* av = (double*)malloc((size_t)n * 3 * sizeof(double));
+        ora_body_viscous_acc(b, b->eta, b->v, av);
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < dim; ++c) b->acc[i * 3 + c] += av[i * 3 + c];
+        free(av);
+    }
     for (int64_t i = 0; i < n; ++i)
         for (int c = 0; c < dim; ++c) b->v[i * 3 + c] += dt * b->acc[i * 3 + c];
     impose_constraints(b);
 
     /* S_d on a randomly chosen step, eta~ = eta / alpha (reading R8) */
-    if (b->p.damping != ORA_DAMP_NONE && b->p.alpha > 0.0 && b->eta > 0.0) {
+    if ((b->p.damping == ORA_DAMP_PARTICLE || b->p.damping == ORA_DAMP_PAIRWISE) && b->p.alpha > 0.0 &&
+        b->eta > 0.0) {
         double phi = ora_phi(b->p.seed, (uint64_t)b->step);
         if (phi < b->p.alpha) {
             ora_body_damp(b, b->eta / b->p.alpha, 0.5 * dt);

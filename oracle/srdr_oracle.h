@@ -28,7 +28,10 @@ extern "C" {
 #endif
 
 enum { ORA_SVK = 0, ORA_NEO_HOOKEAN = 1 };
-enum { ORA_DAMP_NONE = 0, ORA_DAMP_PARTICLE = 1, ORA_DAMP_PAIRWISE = 2 };
+/* ORA_DAMP_EXPLICIT: the comparator of Sec. 3 -- the viscous term of
+ * Eq. damping-term added to dv/dt with eta (no random choice), evaluated
+ * at v^n, under the explicit limit of Eq. viscous-criteria-o */
+enum { ORA_DAMP_NONE = 0, ORA_DAMP_PARTICLE = 1, ORA_DAMP_PAIRWISE = 2, ORA_DAMP_EXPLICIT = 3 };
 enum { ORA_F_RATE = 0, ORA_F_DISPLACEMENT = 1 };
 /* particle flag bits */
 enum { ORA_FLAG_CONSTRAINED = 1, ORA_FLAG_END_LOAD = 2 };
@@ -117,6 +120,9 @@ void ora_body_F_from_u(const ora_body* b, const double* u, double* F_out);
 void ora_body_Fdot(const ora_body* b, const double* v, double* Fdot_out);
 /* dv/dt from a deformation-gradient field (Eq. evaluate-momentum) */
 void ora_body_acc(const ora_body* b, const double* F, double* acc_out);
+/* viscous acceleration of Eq. damping-term for a velocity field v[n][3]:
+ * a_i = (2 eta / m_i) sum_j V_i V_j (v_i - v_j) / r_ij dW/dr (r_ij) */
+void ora_body_viscous_acc(const ora_body* b, double eta, const double* v, double* acc_out);
 /* apply the damping operator S_d (forward then backward sweep) to b's v */
 void ora_body_damp(ora_body* b, double eta_tilde, double dt_loc);
 /* one local update D_i on an arbitrary velocity array v[n][3] */

@@ -320,3 +320,63 @@ def test_damping_is_consistent_with_explicit_viscous_term(scheme, factor):
     assert errs[2] < 0.6 * errs[0]
 
 
+
+
+# ------------------------------------------------------------------ explicit comparator
+@pytest.mark.parametrize("dim", [2, 3])
+def test_explicit_viscous_term_conserves_momentum_and_rigid_motion(dim):
+    """Eq. damping-term is antisymmetric in (i, j): sum_i m_i a_i = 0 for any
+    velocity field, and a uniform velocity is not damped."""
+    ext = (0.008, 0.006, 0.0) if dim == 2 else (0.006, 0.005, 0.004)
+    spec = S.BodySpec(dim=dim, extent=ext, dp=1e-3, clamp_axis=-1)
+    r0, flags, _ = S.jittered(spec, 0.2, 7)
+    b = O.OracleBody(_params(spec), r0[:, :dim], vol_default=spec.vol)
+    rng = np.random.default_rng(3)
+    v = np.zeros((b.n, 3))
+    v[:, :dim] = rng.normal(size=(b.n, dim))
+    a = b.viscous_acc(2.0, v)
+    m = spec.rho0 * spec.vol
+    p = (m * a).sum(axis=0)
+    assert np.abs(p).max() <= 1e-12 * (m * np.abs(a)).sum()
+    u = np.zeros((b.n, 3))
+    u[:, :dim] = rng.normal(size=dim)
+    assert np.abs(b.viscous_acc(2.0, u)).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_explicit_viscous_term_is_half_the_sweep_rate():
+    """The split sweep S_d at eta~ tends to exp(2 dt L) (Sec. 3.1, checked
+    above), so its rate (S_d v - v) / dt tends to twice the explicit
+    acceleration of Eq. damping-term at the same eta: this pins the explicit
+    comparator's term against the implicit scheme's code path."""
+    spec = S.BodySpec(dim=2, extent=(0.008, 0.006, 0), dp=1e-3, clamp_axis=-1)
+    r0, flags, _ = S.jittered(spec, 0.2, 3)
+    b = O.OracleBody(_params(spec), r0[:, :2], vol_default=1e-6)
+    rng = np.random.default_rng(5)
+    v = np.zeros((b.n, 3))
+    v[:, :2] = rng.normal(size=(b.n, 2))
+    want = 2.0 * b.viscous_acc(1.0, v)[:, :2]
+    errs = []
+    for dt in [4e-6, 2e-6, 1e-6]:
+        b.set(O.V, v)
+        b.damp(1.0, dt / 2)
+        rate = (b.v[:, :2] - v[:, :2]) / dt
+        errs.append(np.abs(rate - want).max() / np.abs(want).max())
+    assert errs[0] < 0.05
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 0.6 * errs[0]
+
+
+def test_explicit_time_step_limit():
+    """Eq. viscous-criteria-o: with the explicit comparator dt is at most
+    0.5 h^2 / (nu D), nu = eta / rho0 (here the binding limit)."""
+    spec = S.BodySpec(dim=2, extent=(0.02, 0.01, 0), dp=1e-3, clamp_axis=0, clamp_layers=3,
+                      E=2e6, nu=0.3, beta=5.0, L_char=0.01)
+    r0, flags, _ = S.lattice(spec)
+    b = O.OracleBody(_params(spec, damping=O.DAMP_EXPLICIT), r0[:, :2], vol_default=spec.vol,
+                     flags=flags)
+    eta = O.eta(spec.beta, spec.rho0, spec.E, spec.L_char)
+    limit = 0.5 * spec.h ** 2 / (eta / spec.rho0 * 2)
+    assert b.dt == pytest.approx(limit, rel=1e-14)
+    split = O.OracleBody(_params(spec, damping=O.DAMP_PARTICLE), r0[:, :2], vol_default=spec.vol,
+                         flags=flags)
+    assert split.dt > 10 * b.dt

@@ -106,3 +106,18 @@ def test_pairwise_closed_form_solves_pair_equation():
         want = pair(want, i, j, dt / 2)
     got = b.local_update(i, eta, dt, v)
     assert np.abs(got - want).max() < 1e-13 * np.abs(v).max()
+
+
+def test_explicit_and_split_damping_reach_the_same_state():
+    """The explicit-viscosity comparator (Eq. damping-term under Eq.
+    viscous-criteria-o) and the split random-choice scheme relax the same
+    cantilever to the same static state; the explicit run needs a smaller
+    time step."""
+    base = S.BodySpec(dim=2, extent=(0.06, 0.02, 0), dp=0.002, clamp_axis=0, clamp_layers=3,
+                      material=S.NEO_HOOKEAN, rho0=1000.0, E=2e6, nu=0.3,
+                      gravity=(0, -9.81, 0), beta=0.5, L_char=0.02, alpha=0.2, seed=0)
+    split, _ = _run(base, tol=1e-13)
+    expl, _ = _run(base, tol=1e-12, damping=O.DAMP_EXPLICIT)
+    assert expl.dt < split.dt
+    scale = np.abs(split.u).max()
+    assert np.abs(expl.u - split.u).max() <= 5e-4 * scale
