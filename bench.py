@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["plate", "batched", "served", "block"], default="plate")
+    ap.add_argument("--workload", choices=["plate", "batched", "served", "block", "compare"],
+                    default="plate")
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--served-max-n", type=float, default=2e4)
@@ -442,6 +443,48 @@ def run_block(steps):
     return out
 
 
+def run_compare(tol=1e-8, cap=200000):
+    """The paper's comparison (Sec. 4.1): relaxation of the same cantilevers
+    to KE/KE_max < tol with the split random-choice scheme (alpha = 0.2),
+    damping at every step (alpha = 1), the explicit viscous term under its
+    time-step limit, and no damping; steps, time step, simulated time and
+    device time of each run."""
+    import torch
+
+    from paper_2103_08932_gb300 import srdr
+    from paper_2103_08932_gb300 import synth as S
+    from dataclasses import replace
+    cases = [("2D cantilever 0.2 x 0.02 m, dp = 2 mm, neo-Hookean, FP64", S.cantilever_2d(S.NEO_HOOKEAN),
+              srdr.SRDR_FP64),
+             ("3D plate 0.1 x 0.01 x 0.05 m, dp = 1 mm (plate scaled x0.5), FP32-mixed",
+              S.scaled(S.cantilever_plate_3d(), 0.5), srdr.SRDR_FP32_MIXED)]
+    variants = [("split alpha=0.2", srdr.SRDR_DAMP_PARTICLE, 0.2),
+                ("split alpha=1", srdr.SRDR_DAMP_PARTICLE, 1.0),
+                ("explicit viscosity", srdr.SRDR_DAMP_EXPLICIT, 0.2),
+                ("no damping", srdr.SRDR_DAMP_NONE, 0.2)]
+    out = []
+    for name, spec, prec in cases:
+        rows = []
+        for vname, damping, alpha in variants:
+            b = srdr.Body(srdr.make_desc(replace(spec, alpha=alpha), precision=prec, damping=damping))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            status, steps, ratio = b.relax(tol, cap, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            st = b.stats()
+            u = b.displacement()
+            rows.append({"scheme": vname, "converged": status == srdr.SRDR_OK, "steps": steps,
+                         "ke_ratio": ratio, "dt": st["dt"], "simulated_time_s": steps * st["dt"],
+                         "device_s": e0.elapsed_time(e1) / 1e3, "damped_steps": st["damped_steps"],
+                         "max_abs_displacement_m": float(np.abs(u).max())})
+            b.close()
+        out.append({"case": name, "tol": tol, "step_cap": cap, "runs": rows})
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -450,6 +493,8 @@ def main():
         print(json.dumps({"impl": "gpu", "batched": run_batched(256, 1e3, 2e5, args.steps)}))
     elif args.workload == "block":
         print(json.dumps({"impl": "gpu", "block": run_block(args.steps)}))
+    elif args.workload == "compare":
+        print(json.dumps({"impl": "gpu", "compare": run_compare()}))
     elif args.workload == "served":
         out = [run_served(r, args.requests, 1e3, args.served_max_n, args.served_tol,
                           args.served_max_steps) for r in args.rates]

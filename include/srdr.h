@@ -50,7 +50,7 @@ typedef enum {
 
 enum { SRDR_LINEAR_SVK = 0, SRDR_NEO_HOOKEAN = 1 };
 enum { SRDR_FP64 = 0, SRDR_FP32_MIXED = 1 };
-enum { SRDR_DAMP_NONE = 0, SRDR_DAMP_PARTICLE = 1, SRDR_DAMP_PAIRWISE = 2 };
+enum { SRDR_DAMP_NONE = 0, SRDR_DAMP_PARTICLE = 1, SRDR_DAMP_PAIRWISE = 2, SRDR_DAMP_EXPLICIT = 3 };
 enum { SRDR_FLAG_CONSTRAINED = 1, SRDR_FLAG_END_LOAD = 2 };
 
 /*
@@ -72,7 +72,11 @@ enum { SRDR_FLAG_CONSTRAINED = 1, SRDR_FLAG_END_LOAD = 2 };
  *   eta~ = eta / alpha iff phi_n < alpha, phi_n from Philox4x64-10 with
  *   counter (n, 0, 0, 0) and key (seed, 0), top 53 bits of word 0 / 2^53.
  * damping: SRDR_DAMP_PARTICLE is the particle-by-particle scheme (Sec. 3.1),
- *   SRDR_DAMP_PAIRWISE the pairwise scheme (Sec. 3.2).
+ *   SRDR_DAMP_PAIRWISE the pairwise scheme (Sec. 3.2).  SRDR_DAMP_EXPLICIT is
+ *   the comparator of Sec. 3: the viscous term of Eq. damping-term with eta
+ *   (no random choice, alpha unused) evaluated at v^n and added to dv/dt, with
+ *   dt limited by Eq. viscous-criteria-o, 0.5 h^2 / (nu D), nu = eta / rho0.
+ *   Explicit bodies step alone (batches refuse them).
  * precision: SRDR_FP64 computes everything in FP64; SRDR_FP32_MIXED runs the
  *   neighbour sums, stress and damping in FP32 and keeps the displacement as
  *   an FP32 hi/lo pair (about 48 significant bits) and the kinetic-energy

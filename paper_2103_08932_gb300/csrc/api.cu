@@ -106,7 +106,7 @@ srdr_status check_desc(const srdr_body_desc* d)
         set_error("unknown precision %d", d->precision);
         return SRDR_ERR_INVALID;
     }
-    if (d->damping < SRDR_DAMP_NONE || d->damping > SRDR_DAMP_PAIRWISE) {
+    if (d->damping < SRDR_DAMP_NONE || d->damping > SRDR_DAMP_EXPLICIT) {
         set_error("unknown damping scheme %d", d->damping);
         return SRDR_ERR_INVALID;
     }
@@ -139,7 +139,10 @@ double auto_dt(const srdr_body* b, bool has_end_load)
     double dt = b->h / c;
     if (amax > 0) dt = std::min(dt, sqrt(b->h / amax));
     dt *= 0.6;
-    if (d.damping != SRDR_DAMP_NONE && d.alpha > 0 && b->eta > 0) {
+    if (d.damping == SRDR_DAMP_EXPLICIT) {
+        // Eq. viscous-criteria-o
+        if (b->eta > 0) dt = std::min(dt, 0.5 * b->h * b->h / (b->eta / d.rho0 * b->dim));
+    } else if (d.damping != SRDR_DAMP_NONE && d.alpha > 0 && b->eta > 0) {
         double nut = b->eta / (d.alpha * d.rho0);
         dt = std::min(dt, 50.0 * b->h * b->h / (nut * b->dim));
     }

@@ -704,8 +704,10 @@ srdr_status batch_create(srdr_body* const* bodies, int nb, void* stream, bool ow
     }
     *out = nullptr;
     for (int b = 0; b < nb; ++b)
-        if (!bodies[b] || bodies[b]->dim != bodies[0]->dim || bodies[b]->prec != bodies[0]->prec) {
-            set_error("batched bodies must all exist and share dimension and precision");
+        if (!bodies[b] || bodies[b]->dim != bodies[0]->dim || bodies[b]->prec != bodies[0]->prec ||
+            bodies[b]->desc.damping == SRDR_DAMP_EXPLICIT) {
+            set_error("batched bodies must all exist, share dimension and precision, and use "
+                      "split damping or none");
             return SRDR_ERR_INVALID;
         }
     srdr_batch* bt = new (std::nothrow) srdr_batch();

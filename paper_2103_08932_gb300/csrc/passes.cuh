@@ -448,6 +448,7 @@ __device__ inline double pass_b_epilogue(const StepArgs<T>& a, int i, T (&acc)[D
             T ap = acc[p] * a.inv_rho0 + a.grav[p];
             if (f & SRDR_FLAG_END_LOAD) ap += a.endl[p];
             vi[p] += a.dt * ap;
+            if (a.dvisc) vi[p] += a.dvisc[(size_t)i * 4 + p];
         }
     }
     v4.x = vi[0];
@@ -543,6 +544,36 @@ __global__ void __launch_bounds__(kThreads) k_ke_final(const double* __restrict_
 }
 
 
+// ------------------------------------------------------------------ explicit comparator
+// dv_i = dt (2 eta / m_i) sum_j V_i V_j (v_i - v_j) / r_ij dW/dr (Eq.
+// damping-term at v^n) over the sweep's CSR rows, w_ij = V_i V_j W'(r)/r;
+// the force pass adds it to v* (Sec. 3: the explicit scheme the split
+// random-choice scheme replaces)
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_visc(int n, const int* __restrict__ row_ptr,
+                                                    const int* __restrict__ col, const T* __restrict__ w,
+                                                    const T* __restrict__ v, const T* __restrict__ mass,
+                                                    T c2eta_dt, T* __restrict__ dv, const DevScalars* sc)
+{
+    if (sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const vec4_t<T> vi4 = ld_v4<T>(v, i);
+    const T vi[3] = {vi4.x, vi4.y, vi4.z};
+    T e[3] = {0, 0, 0};
+    for (int k = __ldg(row_ptr + i); k < __ldg(row_ptr + i + 1); ++k) {
+        const vec4_t<T> vj4 = ld_v4<T>(v, __ldg(col + k));
+        const T vj[3] = {vj4.x, vj4.y, vj4.z};
+        const T wk = __ldg(w + k);
+#pragma unroll
+        for (int d = 0; d < D; ++d) e[d] = fma_t(wk, sub_t(vi[d], vj[d]), e[d]);
+    }
+    const T s = c2eta_dt / mass[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dv[(size_t)i * 4 + d] = d < D ? s * e[d] : T(0);
+    dv[(size_t)i * 4 + 3] = T(0);
+}
+
 // ------------------------------------------------------------------ host: kernel arguments
 template <typename T>
 StepArgs<T> make_step_args(srdr_body* b)
@@ -559,6 +590,7 @@ StepArgs<T> make_step_args(srdr_body* b)
     a.B0 = static_cast<const T*>(b->B0);
     a.PB = static_cast<T*>(b->PB);
     a.Gs = static_cast<const T*>(b->Gs);
+    a.dvisc = static_cast<const T*>(b->dvisc);
     a.v = static_cast<T*>(b->v);
     a.u = b->u;
     a.uhi = b->uhi;

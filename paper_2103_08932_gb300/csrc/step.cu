@@ -207,9 +207,17 @@ template <typename T, int D, int MAT>
 srdr_status steps_typed(srdr_body* b, int64_t nsteps)
 {
     cudaStream_t st = b->stream;
+    const bool explicit_visc = b->desc.damping == SRDR_DAMP_EXPLICIT && b->eta > 0.0;
+    if (explicit_visc && !b->dvisc) {
+        T* dv = nullptr;
+        SRDR_TRY(dalloc(b, &dv, (size_t)4 * b->n));
+        b->dvisc = dv;
+    }
     StepArgs<T> a = make_step_args<T>(b);
     const int nb = nblocks(b->n);
-    const bool damping = b->desc.damping != SRDR_DAMP_NONE && b->desc.alpha > 0.0 && b->eta > 0.0;
+    const bool damping = (b->desc.damping == SRDR_DAMP_PARTICLE || b->desc.damping == SRDR_DAMP_PAIRWISE) &&
+                         b->desc.alpha > 0.0 && b->eta > 0.0;
+    const T c2eta_dt = (T)(2.0 * b->eta * b->dt);
     if (damping && !b->sbm) SRDR_TRY(prepare_sweep(b));
     SweepArgs<T> sw = make_sweep_args<T>(b);
     SweepLaunch<T, D> sl;
@@ -254,6 +262,16 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
             k_pass_a<T, D, MAT><<<nb, kThreads, 0, st>>>(a);
         prof_end(b, SRDR_K_PASS_A, ev);
         counted(SRDR_K_PASS_A, 1);
+        if (explicit_visc) {
+            // the explicit comparator's damping, at v^n, before the force pass
+            prof_begin(b, SRDR_K_SWEEP, &ev);
+            k_visc<T, D><<<nb, kThreads, 0, st>>>((int)b->n, b->row_ptr, b->col,
+                                                  static_cast<const T*>(b->w), static_cast<const T*>(b->v),
+                                                  static_cast<const T*>(b->mass), c2eta_dt,
+                                                  static_cast<T*>(b->dvisc), b->sc);
+            prof_end(b, SRDR_K_SWEEP, ev);
+            counted(SRDR_K_SWEEP, 1);
+        }
         prof_begin(b, SRDR_K_PASS_B, &ev);
         if (tiled)
             k_pass_b_tiled<T, D><<<b->nbricks, kTileThreads, smem_b, st>>>(a, tl, damp ? 0 : 1);

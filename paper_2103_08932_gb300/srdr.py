@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "OK", -1: "INVALID", -2: "NO_MEMORY", -3: "CUDA", -4: "NOT_CO
 
 SRDR_LINEAR_SVK, SRDR_NEO_HOOKEAN = 0, 1
 SRDR_FP64, SRDR_FP32_MIXED = 0, 1
-SRDR_DAMP_NONE, SRDR_DAMP_PARTICLE, SRDR_DAMP_PAIRWISE = 0, 1, 2
+SRDR_DAMP_NONE, SRDR_DAMP_PARTICLE, SRDR_DAMP_PAIRWISE, SRDR_DAMP_EXPLICIT = 0, 1, 2, 3
 SRDR_FLAG_CONSTRAINED, SRDR_FLAG_END_LOAD = 1, 2
 SRDR_FIELD_PB, SRDR_FIELD_B0 = 0, 1
 

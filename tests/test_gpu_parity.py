@@ -353,3 +353,58 @@ def test_pass_mapping_rejects_bad_arguments():
         with pytest.raises(srdr.SrdrError) as e:
             b.pass_mapping(*args)
         assert e.value.status == srdr.SRDR_ERR_INVALID
+
+
+# ------------------------------------------------------------------ explicit comparator
+@pytest.mark.parametrize("spec", [S.cantilever_2d(S.NEO_HOOKEAN), SMALL3D])
+def test_explicit_comparator_fp64_matches_oracle(spec):
+    """The explicit-viscosity comparator (Eq. damping-term at v^n, dt from
+    Eq. viscous-criteria-o): same time step as the oracle and FP64 parity at
+    every step."""
+    ob = oracle_for(spec, damping=O.DAMP_EXPLICIT)
+    gb = gpu_for(spec, damping=srdr.SRDR_DAMP_EXPLICIT)
+    assert gb.stats()["dt"] == pytest.approx(ob.dt, rel=1e-14)
+    worst_v = worst_u = 0.0
+    for _ in range(60):
+        ob.step(1)
+        gb.step(1)
+        worst_v = max(worst_v, rel(gb.velocity(), ob.v))
+        worst_u = max(worst_u, rel(gb.displacement(), ob.u))
+    assert gb.stats()["damped_steps"] == 0
+    assert worst_v <= 1e-10 and worst_u <= 1e-10
+
+
+def test_explicit_comparator_fp32_mixed():
+    spec = S.cantilever_2d(S.NEO_HOOKEAN)
+    ob = oracle_for(spec, damping=O.DAMP_EXPLICIT)
+    gb = gpu_for(spec, precision=srdr.SRDR_FP32_MIXED, damping=srdr.SRDR_DAMP_EXPLICIT)
+    worst = 0.0
+    for _ in range(100):
+        ob.step(1)
+        gb.step(1)
+        worst = max(worst, rel(gb.velocity(), ob.v))
+    assert worst <= 2e-5
+
+
+def test_explicit_and_split_relax_to_the_same_state_on_gpu():
+    """Relaxed on the GPU, the explicit comparator and the split random-choice
+    scheme reach the same static state; the explicit run needs a smaller time
+    step (Eq. viscous-criteria-o against Eq. viscous-criteria)."""
+    base = S.BodySpec(dim=2, extent=(0.06, 0.02, 0), dp=0.002, clamp_axis=0, clamp_layers=3,
+                      material=S.NEO_HOOKEAN, rho0=1000.0, E=2e6, nu=0.3,
+                      gravity=(0, -9.81, 0), beta=0.5, L_char=0.02, alpha=0.2, seed=0)
+    split = gpu_for(base)
+    _, n_split, _ = split.relax(1e-13, 10 ** 6)
+    expl = gpu_for(base, damping=srdr.SRDR_DAMP_EXPLICIT)
+    _, n_expl, _ = expl.relax(1e-12, 10 ** 6)
+    assert expl.stats()["dt"] < split.stats()["dt"]
+    u0 = split.displacement()
+    assert np.abs(expl.displacement() - u0).max() <= 5e-4 * np.abs(u0).max()
+
+
+def test_batch_refuses_explicit_bodies():
+    a = gpu_for(SMALL2D)
+    b = gpu_for(SMALL2D, damping=srdr.SRDR_DAMP_EXPLICIT)
+    with pytest.raises(srdr.SrdrError) as e:
+        srdr.Batch([a, b])
+    assert e.value.status == srdr.SRDR_ERR_INVALID
