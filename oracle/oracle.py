@@ -53,6 +53,7 @@ class _Params(C.Structure):
         ("alpha", C.c_double), ("seed", C.c_uint64),
         ("damping", C.c_int), ("f_form", C.c_int),
         ("dt", C.c_double),
+        ("twist", C.c_double * 4),
     ]
 
 
@@ -102,6 +103,7 @@ def lib():
         L.ora_body_acc.argtypes = [p, p, p]
         L.ora_body_damp.argtypes = [p, d, d]
         L.ora_body_viscous_acc.argtypes = [p, d, p, p]
+        L.ora_twist_force.argtypes = [p, p, p]
         L.ora_body_local_update.argtypes = [p, i64, d, d, p]
     return _lib
 
@@ -160,6 +162,15 @@ def philox4x64_10(counter, key):
     return out
 
 
+def twist_force(params, r):
+    """Rotational body force of reading R17 at reference position r."""
+    ra = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(3))
+    out = np.zeros(3)
+    cp = params.to_c()
+    lib().ora_twist_force(C.byref(cp), _ptr(ra), _ptr(out))
+    return out
+
+
 def phi(seed, step):
     return lib().ora_phi(seed, step)
 
@@ -203,13 +214,15 @@ class Params:
     damping: int = DAMP_PARTICLE
     f_form: int = F_RATE
     dt: float = 0.0
+    twist: tuple = (0.0, 0.0, 0.0, 0.0)  # (gamma0, L, y_c, z_c), reading R17
 
     def to_c(self) -> _Params:
         g = list(self.gravity) + [0.0] * (3 - len(self.gravity))
         e = list(self.end_load) + [0.0] * (3 - len(self.end_load))
         return _Params(self.dim, self.material, self.rho0, self.E, self.nu, self.h,
                        (C.c_double * 3)(*g), (C.c_double * 3)(*e), self.beta, self.L_char,
-                       self.alpha, self.seed, self.damping, self.f_form, self.dt)
+                       self.alpha, self.seed, self.damping, self.f_form, self.dt,
+                       (C.c_double * 4)(*self.twist))
 
 
 class OracleBody:

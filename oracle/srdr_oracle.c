@@ -33,6 +33,14 @@
  *   R12 dt fixed per body: Eq. time-step-criterion with |v|max = 0 and
  *       |a|max = the largest body-force magnitude, min'd with the implicit
  *       viscous limit 50 h^2 / (nu~ D), nu~ = eta / (alpha rho0).
+ *   R17 Twisting body force (Sec. 4.2): the printed g = (0, y gamma, z gamma)
+ *       is radial, at odds with the "rotational body-force" that "twists"
+ *       the cantilever.  Read it as the rotation about the cantilever axis
+ *       (y_c, z_c): g = gamma (0, -(z - z_c), y - y_c), gamma = gamma0
+ *       sin(pi x / (2L)), x from the clamped face; gamma0 = 20 g / H with the
+ *       thickness H for "h" (as in the survey's reading of h / dp).  It is
+ *       added to gravity on every particle; dt's |a|max is the largest
+ *       |g + end load + g_t| over the particles.
  *   R16 Explicit-viscosity comparator (ORA_DAMP_EXPLICIT, Sec. 3): the term of
  *       Eq. damping-term with eta itself (no random choice) is evaluated at
  *       v^n and added to the acceleration of S_m; dt is min'd with the
@@ -524,6 +532,16 @@ static double body_dt(const ora_body* b)
     double K = b->lambda + 2.0 * b->mu / 3.0;
     double c = sqrt(K / p->rho0);
     double amax = vec_norm(dim, p->gravity);
+    if (p->twist[0] != 0.0) {
+        for (int64_t i = 0; i < b->n; ++i) {
+            double t[3], a[3];
+            ora_twist_force(p, b->r0 + i * 3, t);
+            for (int k = 0; k < 3; ++k)
+                a[k] = p->gravity[k] + ((b->flags[i] & ORA_FLAG_END_LOAD) ? p->end_load[k] : 0.0) + t[k];
+            double m = vec_norm(dim, a);
+            if (m > amax) amax = m;
+        }
+    }
     for (int64_t i = 0; i < b->n; ++i)
         if (b->flags[i] & ORA_FLAG_END_LOAD) {
             double a[3];
@@ -742,8 +760,10 @@ void ora_body_acc(const ora_body* b, const double* F, double* acc_out)
                 a[r] += b->vol[i] * b->vol[j] * s;
             }
         }
+        double tw[3] = {0, 0, 0};
+        if (b->p.twist[0] != 0.0) ora_twist_force(&b->p, b->r0 + i * 3, tw);
         for (int r = 0; r < 3; ++r) {
-            double extra = b->p.gravity[r];
+            double extra = b->p.gravity[r] + tw[r];
             if (b->flags[i] & ORA_FLAG_END_LOAD) extra += b->p.end_load[r];
             acc_out[i * 3 + r] = (r < dim ? 2.0 / b->mass[i] * a[r] : 0.0) + (r < dim ? extra : 0.0);
         }
@@ -758,6 +778,15 @@ static double coeff_B(const ora_body* b, int64_t i, int64_t k, double eta, doubl
 {
     int64_t j = b->col[k];
     return 2.0 * eta * b->vol[i] * b->vol[j] * (1.0 / b->rij[k]) * b->dW[k] * dt;
+}
+
+/* Eq. rotation-body-force with reading R17 */
+void ora_twist_force(const ora_params* p, const double r[3], double out[3])
+{
+    double gamma = p->twist[0] * sin(ORA_PI * r[0] / (2.0 * p->twist[1]));
+    out[0] = 0.0;
+    out[1] = -gamma * (r[2] - p->twist[3]);
+    out[2] = gamma * (r[1] - p->twist[2]);
 }
 
 /* Eq. damping-term: a_i = (2 eta / m_i) sum_j V_i V_j v_ij / r_ij (dW/dr)_ij */

@@ -49,6 +49,10 @@ typedef struct {
     int damping;           /* ORA_DAMP_* */
     int f_form;            /* ORA_F_RATE (paper, Sec. 2.3) | ORA_F_DISPLACEMENT */
     double dt;             /* > 0: use this time step; 0: Eq. time-step-criterion */
+    /* rotational body force of the twisting cantilever (Sec. 4.2, Eq.
+     * rotation-body-force, reading R17): twist = (gamma0, L, y_c, z_c),
+     * g_t = gamma0 sin(pi x / (2 L)) (0, -(z - z_c), y - y_c); gamma0 = 0: none */
+    double twist[4];
 } ora_params;
 
 /* ---- closed pieces ---------------------------------------------------- */
@@ -120,6 +124,8 @@ void ora_body_F_from_u(const ora_body* b, const double* u, double* F_out);
 void ora_body_Fdot(const ora_body* b, const double* v, double* Fdot_out);
 /* dv/dt from a deformation-gradient field (Eq. evaluate-momentum) */
 void ora_body_acc(const ora_body* b, const double* F, double* acc_out);
+/* rotational body force of reading R17 at reference position r (3 doubles) */
+void ora_twist_force(const ora_params* p, const double r[3], double out[3]);
 /* viscous acceleration of Eq. damping-term for a velocity field v[n][3]:
  * a_i = (2 eta / m_i) sum_j V_i V_j (v_i - v_j) / r_ij dW/dr (r_ij) */
 void ora_body_viscous_acc(const ora_body* b, double eta, const double* v, double* acc_out);

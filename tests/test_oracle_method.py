@@ -380,3 +380,51 @@ def test_explicit_time_step_limit():
     split = O.OracleBody(_params(spec, damping=O.DAMP_PARTICLE), r0[:, :2], vol_default=spec.vol,
                          flags=flags)
     assert split.dt > 10 * b.dt
+
+
+# ------------------------------------------------------------------ twisting body force
+def test_twist_force_is_a_rotation_about_the_axis():
+    """Reading R17 of Eq. rotation-body-force: the force is perpendicular to
+    the radius from the axis (y_c, z_c), has no axial component, grows as
+    sin(pi x / 2L) from zero at the clamped face to gamma0 r at x = L, and
+    turns counter-clockwise about +x for gamma0 > 0."""
+    p = O.Params(dim=3, twist=(50.0, 0.2, 0.01, 0.05))
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        r = rng.uniform([0, 0, 0], [0.2, 0.02, 0.1])
+        g = O.twist_force(p, r)
+        rad = np.array([0.0, r[1] - 0.01, r[2] - 0.05])
+        assert g[0] == 0.0
+        assert abs(g @ rad) <= 1e-15 * np.linalg.norm(g) * np.linalg.norm(rad) + 1e-300
+        gamma = 50.0 * np.sin(np.pi * r[0] / 0.4)
+        assert np.linalg.norm(g) == pytest.approx(abs(gamma) * np.linalg.norm(rad), rel=1e-13)
+        assert np.cross(rad, g)[0] == pytest.approx(gamma * (rad @ rad), rel=1e-12)
+    assert np.abs(O.twist_force(p, [0.0, 0.0, 0.0])).max() == 0.0
+    tip = O.twist_force(p, [0.2, 0.02, 0.05])
+    assert tip[2] == pytest.approx(50.0 * 0.01, rel=1e-14)
+
+
+def test_twist_force_drives_the_first_step():
+    """A body at rest has no stress, so its first undamped step gives every
+    free particle v = dt (g + g_t(r0_i)); the time step sees the largest
+    body-force magnitude."""
+    spec = S.BodySpec(dim=3, extent=(0.008, 0.004, 0.004), dp=1e-3, clamp_axis=0, clamp_layers=3,
+                      gravity=(0.0, -9.81, 0.0))
+    tw = (2000.0, 0.008, 0.002, 0.002)
+    r0, flags, _ = S.lattice(spec)
+    b = O.OracleBody(_params(spec, damping=O.DAMP_NONE, twist=tw), r0, vol_default=spec.vol,
+                     flags=flags)
+    plain = O.OracleBody(_params(spec, damping=O.DAMP_NONE), r0, vol_default=spec.vol, flags=flags)
+    p = _params(spec, twist=tw)
+    force = np.array([O.twist_force(p, r) for r in r0]) + np.array(spec.gravity)
+    assert b.dt == plain.dt  # the acoustic limit binds at this load
+    # a load large enough for the body-force limit to bind: the largest |g + g_t|
+    big = (2e9, 0.008, 0.002, 0.002)
+    pb = _params(spec, damping=O.DAMP_NONE, twist=big)
+    fb = np.array([O.twist_force(pb, r) for r in r0]) + np.array(spec.gravity)
+    bb = O.OracleBody(pb, r0, vol_default=spec.vol, flags=flags)
+    assert bb.dt == pytest.approx(0.6 * np.sqrt(spec.h / np.linalg.norm(fb, axis=1).max()), rel=1e-14)
+    b.step(1)
+    free = (flags & O.FLAG_CONSTRAINED) == 0
+    assert np.abs(b.v[free] - b.dt * force[free]).max() <= 1e-12 * np.abs(b.dt * force).max()
+    assert np.abs(b.v[~free]).max() == 0.0
