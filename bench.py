@@ -444,7 +444,7 @@ def run_block(steps):
 
 
 def run_compare(tol=1e-8, cap=200000):
-    """The paper's comparison (Sec. 4.1): relaxation of the same cantilevers
+    """The paper's comparisons (Sec. 4.1, 4.2): relaxation of the same bodies
     to KE/KE_max < tol with the split random-choice scheme (alpha = 0.2),
     damping at every step (alpha = 1), the explicit viscous term under its
     time-step limit, and no damping; steps, time step, simulated time and
@@ -457,7 +457,9 @@ def run_compare(tol=1e-8, cap=200000):
     cases = [("2D cantilever 0.2 x 0.02 m, dp = 2 mm, neo-Hookean, FP64", S.cantilever_2d(S.NEO_HOOKEAN),
               srdr.SRDR_FP64),
              ("3D plate 0.1 x 0.01 x 0.05 m, dp = 1 mm (plate scaled x0.5), FP32-mixed",
-              S.scaled(S.cantilever_plate_3d(), 0.5), srdr.SRDR_FP32_MIXED)]
+              S.scaled(S.cantilever_plate_3d(), 0.5), srdr.SRDR_FP32_MIXED),
+             ("3D twisting cantilever 0.2 x 0.02 x 0.02 m, dp = 1 mm, rotational body force, "
+              "FP32-mixed", S.twisting_cantilever_3d(), srdr.SRDR_FP32_MIXED)]
     variants = [("split alpha=0.2", srdr.SRDR_DAMP_PARTICLE, 0.2),
                 ("split alpha=1", srdr.SRDR_DAMP_PARTICLE, 1.0),
                 ("explicit viscosity", srdr.SRDR_DAMP_EXPLICIT, 0.2),

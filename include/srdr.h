@@ -84,6 +84,12 @@ enum { SRDR_FLAG_CONSTRAINED = 1, SRDR_FLAG_END_LOAD = 2 };
  * dt: > 0 fixes the time step; 0 uses Eq. time-step-criterion with
  *   |v|max = 0 and |a|max = the largest body force, min'd with the implicit
  *   viscous limit 50 h^2 / (nu~ D) of Eq. viscous-criteria, nu~ = eta/(alpha rho0).
+ * twist: the rotational body force of the twisting cantilever (Sec. 4.2,
+ *   Eq. rotation-body-force) read as a rotation about the axis through
+ *   (y, z) = (twist[2], twist[3]): g_t = twist[0] sin(pi x / (2 twist[1]))
+ *   (0, -(z - twist[3]), y - twist[2]) per unit mass, x from the clamped face
+ *   (the printed (0, y gamma, z gamma) is radial, not rotational).  Added to
+ *   gravity on every particle; 3D only; twist[0] = 0: none.
  */
 typedef struct {
     int dim;
@@ -104,6 +110,7 @@ typedef struct {
     int damping;
     int precision;
     double dt;
+    double twist[4];
 } srdr_body_desc;
 
 typedef struct srdr_body srdr_body;

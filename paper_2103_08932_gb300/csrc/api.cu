@@ -114,13 +114,28 @@ srdr_status check_desc(const srdr_body_desc* d)
         set_error("alpha must lie in [0, 1]");
         return SRDR_ERR_INVALID;
     }
+    if (d->twist[0] != 0.0 && (d->dim != 3 || !(d->twist[1] > 0.0) || !std::isfinite(d->twist[0]) ||
+                               !std::isfinite(d->twist[2]) || !std::isfinite(d->twist[3]))) {
+        set_error("the twisting body force needs dim 3, a finite amplitude and axis, and L > 0");
+        return SRDR_ERR_INVALID;
+    }
     return SRDR_OK;
 }
 
 // time step: 0.6 min(h / c, sqrt(h / |a|max)) with c = sqrt(K / rho0)
 // (Eq. time-step-criterion at |v|max = 0), and the implicit viscous limit
 // 50 h^2 / (nu~ D), nu~ = eta / (alpha rho0) (Eq. viscous-criteria).
-double auto_dt(const srdr_body* b, bool has_end_load)
+// rotational body force of the twisting cantilever (the reading of Eq.
+// rotation-body-force stated in srdr.h)
+void twist_force(const srdr_body_desc& d, const double* r, double* g)
+{
+    const double gamma = d.twist[0] * sin(3.14159265358979323846 * r[0] / (2.0 * d.twist[1]));
+    g[0] = 0.0;
+    g[1] = -gamma * (r[2] - d.twist[3]);
+    g[2] = gamma * (r[1] - d.twist[2]);
+}
+
+double auto_dt(const srdr_body* b, bool has_end_load, int64_t n, const double* r0, const uint8_t* flags)
 {
     const srdr_body_desc& d = b->desc;
     double K = b->lambda + 2.0 * b->mu / 3.0;
@@ -135,6 +150,16 @@ double auto_dt(const srdr_body* b, bool has_end_load)
         double ge[3] = {d.gravity[0] + d.end_load[0], d.gravity[1] + d.end_load[1],
                         d.gravity[2] + d.end_load[2]};
         amax = std::max(amax, norm(ge));
+    }
+    if (d.twist[0] != 0.0) {
+        // the largest |g + end load + g_t| over the particles
+        for (int64_t i = 0; i < n; ++i) {
+            double t[3], a[3];
+            twist_force(d, r0 + i * 3, t);
+            const bool end = flags && (flags[i] & SRDR_FLAG_END_LOAD);
+            for (int k = 0; k < 3; ++k) a[k] = d.gravity[k] + (end ? d.end_load[k] : 0.0) + t[k];
+            amax = std::max(amax, norm(a));
+        }
     }
     double dt = b->h / c;
     if (amax > 0) dt = std::min(dt, sqrt(b->h / amax));
@@ -180,7 +205,7 @@ srdr_status create_common(const srdr_body_desc* desc, int64_t n, const double* r
     bool has_end = false;
     if (flags)
         for (int64_t i = 0; i < n && !has_end; ++i) has_end = (flags[i] & SRDR_FLAG_END_LOAD) != 0;
-    b->dt = desc->dt > 0 ? desc->dt : auto_dt(b, has_end);
+    b->dt = desc->dt > 0 ? desc->dt : auto_dt(b, has_end, n, r0, flags);
 
     srdr_status st = dalloc(b, &b->sc, 1);
     if (st == SRDR_OK) {

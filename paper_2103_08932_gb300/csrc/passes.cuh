@@ -446,6 +446,7 @@ __device__ inline double pass_b_epilogue(const StepArgs<T>& a, int i, T (&acc)[D
 #pragma unroll
         for (int p = 0; p < D; ++p) {
             T ap = acc[p] * a.inv_rho0 + a.grav[p];
+            if (a.bf) ap += a.bf[(size_t)i * 4 + p];
             if (f & SRDR_FLAG_END_LOAD) ap += a.endl[p];
             vi[p] += a.dt * ap;
             if (a.dvisc) vi[p] += a.dvisc[(size_t)i * 4 + p];
@@ -591,6 +592,7 @@ StepArgs<T> make_step_args(srdr_body* b)
     a.PB = static_cast<T*>(b->PB);
     a.Gs = static_cast<const T*>(b->Gs);
     a.dvisc = static_cast<const T*>(b->dvisc);
+    a.bf = static_cast<const T*>(b->bf);
     a.v = static_cast<T*>(b->v);
     a.u = b->u;
     a.uhi = b->uhi;

@@ -270,6 +270,23 @@ __global__ void k_gsum(int n, const int* __restrict__ row_ptr, const int* __rest
     for (int p = 0; p < 3; ++p) Gs[(size_t)p * n + i] = (T)G[p];
 }
 
+// rotational body force of the twisting cantilever per particle (sorted
+// order), from the FP64 reference positions: g_t = gamma0 sin(pi x / 2L)
+// (0, -(z - z_c), y - y_c)
+template <typename T>
+__global__ void k_twist(int n, const double* __restrict__ r0, double g0, double L, double yc, double zc,
+                        T* __restrict__ bf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = r0[i], y = r0[(size_t)n + i], z = r0[(size_t)2 * n + i];
+    const double gamma = g0 * sin(3.14159265358979323846 * x / (2.0 * L));
+    bf[(size_t)i * 4 + 0] = T(0);
+    bf[(size_t)i * 4 + 1] = (T)(-gamma * (z - zc));
+    bf[(size_t)i * 4 + 2] = (T)(gamma * (y - yc));
+    bf[(size_t)i * 4 + 3] = T(0);
+}
+
 // velocity records (0, 0, 0, 1/m)
 template <typename T>
 __global__ void k_v_init(int n, const T* __restrict__ minv, T* __restrict__ v)
@@ -743,6 +760,13 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_TRY(dalloc(b, &v, (size_t)n * 4));
     b->v = v;
     k_v_init<T><<<nblocks(n), kThreads, 0, st>>>(n, minv, v);
+    if (b->desc.twist[0] != 0.0) {
+        T* bf = nullptr;
+        SRDR_TRY(dalloc(b, &bf, (size_t)n * 4));
+        b->bf = bf;
+        k_twist<T><<<nblocks(n), kThreads, 0, st>>>(n, b->r0, b->desc.twist[0], b->desc.twist[1],
+                                                   b->desc.twist[2], b->desc.twist[3], bf);
+    }
     b->ke_blocks = b->nslices;  // one FP64 partial per 32-particle slice
     SRDR_TRY(dalloc(b, &b->ke_part, b->ke_blocks));
     SRDR_CK(cudaMemsetAsync(b->ke_part, 0, sizeof(double) * b->ke_blocks, st));

@@ -92,6 +92,7 @@ struct StepArgs {
     T* __restrict__ PB;         // [pb_chunks][n] 16-byte chunks
     const T* __restrict__ Gs;   // [3][n]
     const T* __restrict__ dvisc; // [n][4] explicit comparator: dt a_visc(v^n), else null
+    const T* __restrict__ bf;    // [n][4] per-particle body force (twist), else null
     T* __restrict__ v;          // [n][4] (vx, vy, vz, 1/m)
     double* __restrict__ u;     // [3][n] FP64 mode
     float* __restrict__ uhi;    // [n][4] FP32 mode, u = hi + lo
@@ -202,6 +203,7 @@ struct srdr_body {
     void* bg = nullptr;              // T [3][bslots] pair gradients
     double* ke_pp = nullptr;         // [n] kinetic energy per particle (tiled pass B)
     void* dvisc = nullptr;           // T [n][4] explicit comparator: dt a_visc(v^n)
+    void* bf = nullptr;              // T [n][4] rotational body force per particle (twist)
     int sweep_cells_per_warp = 2;    // cells per warp of the sweep kernel (1, 2, 4)
     int sweep_warps_per_block = 1;   // warps per block of the sweep kernel (1, 4)
     int sweep_tuned = 0;

@@ -80,6 +80,7 @@ class srdr_body_desc(C.Structure):
         ("damping", C.c_int),
         ("precision", C.c_int),
         ("dt", C.c_double),
+        ("twist", C.c_double * 4),
     ]
 
 
@@ -184,6 +185,7 @@ def make_desc(spec, precision=SRDR_FP64, damping=SRDR_DAMP_PARTICLE, dt=0.0) -> 
     d.damping = damping
     d.precision = precision
     d.dt = dt
+    d.twist = (C.c_double * 4)(*getattr(spec, "twist", (0.0, 0.0, 0.0, 0.0)))
     return d
 
 

@@ -56,6 +56,8 @@ class BodySpec:
     L_char: float = 0.02
     alpha: float = 0.2
     seed: int = 0
+    # rotational body force (gamma0, L, y_c, z_c) of the twisting cantilever
+    twist: tuple = (0.0, 0.0, 0.0, 0.0)
 
     def counts(self):
         n = [1, 1, 1]
@@ -137,6 +139,17 @@ def cantilever_plate_3d(dp: float = 1e-3) -> BodySpec:
     return BodySpec(dim=3, extent=(0.2, 0.02, 0.1), dp=dp, clamp_axis=0, clamp_layers=3,
                     material=NEO_HOOKEAN, rho0=1000.0, E=2e6, nu=0.3, gravity=(0.0, -9.81, 0.0),
                     beta=0.2, L_char=0.02, alpha=0.2, seed=1)
+
+
+def twisting_cantilever_3d(dp: float = 1e-3) -> BodySpec:
+    """Twisting cantilever: a 0.2 m beam of square 0.02 m section, dp = 1 mm
+    (200 x 20 x 20 body particles + 3 clamped layers, 81,200 in all),
+    neo-Hookean as the bending case, no gravity, the rotational body force
+    about the beam axis with gamma0 = 20 g / H (g = 9.8, H = 0.02 m), seed 5."""
+    H = 0.02
+    return BodySpec(dim=3, extent=(0.2, H, H), dp=dp, clamp_axis=0, clamp_layers=3,
+                    material=NEO_HOOKEAN, rho0=1000.0, E=2e6, nu=0.3, gravity=(0.0, 0.0, 0.0),
+                    beta=0.2, L_char=H, alpha=0.2, seed=5, twist=(20 * 9.8 / H, 0.2, H / 2, H / 2))
 
 
 def compression_block_3d(dp: float = 8e-4, edge: float = 0.1) -> BodySpec:

@@ -30,7 +30,8 @@ def oracle_for(spec, r0=None, flags=None, u0=None, damping=O.DAMP_PARTICLE, dt=0
         r0, flags, u0 = S.lattice(spec)
     p = O.Params(dim=spec.dim, material=spec.material, rho0=spec.rho0, E=spec.E, nu=spec.nu,
                  h=spec.h, gravity=spec.gravity, end_load=spec.end_load, beta=spec.beta,
-                 L_char=spec.L_char, alpha=spec.alpha, seed=spec.seed, damping=damping, dt=dt)
+                 L_char=spec.L_char, alpha=spec.alpha, seed=spec.seed, damping=damping, dt=dt,
+                 twist=spec.twist)
     for k, v in kw.items():
         setattr(p, k, v)
     has_u0 = u0 is not None and np.abs(u0).max() > 0
@@ -407,4 +408,45 @@ def test_batch_refuses_explicit_bodies():
     b = gpu_for(SMALL2D, damping=srdr.SRDR_DAMP_EXPLICIT)
     with pytest.raises(srdr.SrdrError) as e:
         srdr.Batch([a, b])
+    assert e.value.status == srdr.SRDR_ERR_INVALID
+
+
+# ------------------------------------------------------------------ twisting body force
+TWIST3D = S.BodySpec(dim=3, extent=(0.012, 0.004, 0.004), dp=1e-3, clamp_axis=0, clamp_layers=3,
+                     material=S.NEO_HOOKEAN, gravity=(0.0, 0.0, 0.0), beta=0.2, L_char=0.004,
+                     alpha=0.5, seed=3, twist=(20 * 9.8 / 0.004, 0.012, 0.002, 0.002))
+
+
+@pytest.mark.parametrize("precision,tol", [(srdr.SRDR_FP64, 1e-10), (srdr.SRDR_FP32_MIXED, 2e-5)])
+def test_twisting_body_force_matches_oracle(precision, tol):
+    """The rotational body force of the twisting cantilever (Sec. 4.2):
+    per-step velocity and displacement against the oracle."""
+    ob = oracle_for(TWIST3D)
+    gb = gpu_for(TWIST3D, precision=precision)
+    assert gb.stats()["dt"] == pytest.approx(ob.dt, rel=1e-14)
+    worst = 0.0
+    for _ in range(40):
+        ob.step(1)
+        gb.step(1)
+        worst = max(worst, rel(gb.velocity(), ob.v), rel(gb.displacement(), ob.u))
+    assert ob.damped_steps == gb.stats()["damped_steps"] > 0
+    assert worst <= tol
+
+
+def test_twisted_body_in_a_batch_equals_alone():
+    alone = gpu_for(TWIST3D, precision=srdr.SRDR_FP32_MIXED)
+    alone.step(30)
+    a = gpu_for(TWIST3D, precision=srdr.SRDR_FP32_MIXED)
+    b = gpu_for(SMALL3D, precision=srdr.SRDR_FP32_MIXED)
+    batch = srdr.Batch([a, b])
+    batch.step(30)
+    assert np.array_equal(a.velocity(), alone.velocity())
+    assert np.array_equal(a.displacement(), alone.displacement())
+
+
+def test_twist_needs_3d():
+    from dataclasses import replace
+    bad = replace(SMALL2D, twist=(100.0, 0.05, 0.005, 0.0))
+    with pytest.raises(srdr.SrdrError) as e:
+        gpu_for(bad)
     assert e.value.status == srdr.SRDR_ERR_INVALID
