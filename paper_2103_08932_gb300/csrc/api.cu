@@ -383,6 +383,8 @@ void srdr_body_destroy(srdr_body* b)
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
     for (void* p : b->allocs) cudaFree(p);
     b->allocs.clear();
     for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
@@ -567,6 +569,10 @@ srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp, int warps_per_block
                   "and warps per block 1, 4");
         return SRDR_ERR_INVALID;
     }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);  // captured with the old mapping
+        b->graph = nullptr;
+    }
     if (autotune) {
         b->sweep_tuned = 0;
     } else {
@@ -599,6 +605,10 @@ srdr_status srdr_body_pass_mapping(srdr_body* b, int mapping, int bx, int by, in
         b->bg = nullptr;
         b->ke_pp = nullptr;
         b->bricks_built = 0;
+    }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);  // captured with the old mapping
+        b->graph = nullptr;
     }
     b->brick[0] = bx;
     b->brick[1] = by;

@@ -500,6 +500,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kThreads, 3) k_pass_b(StepArgs<T> a, int final_step)
 {
     if (a.sc->done) return;
+    if (a.dflag) final_step = *a.dflag == 0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double ke = i < a.n ? pass_b_particle<T, D>(a, i, final_step) : 0.0;
     if (final_step) slice_partial_store(ke, a.ke_part, i, a.n);
@@ -530,7 +531,7 @@ __device__ inline double finish_particle(const StepArgs<T>& a, int i)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_finish(StepArgs<T> a)
 {
-    if (a.sc->done) return;
+    if (a.sc->done || (a.dflag && *a.dflag == 0)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double ke = i < a.n ? finish_particle<T>(a, i) : 0.0;
     slice_partial_store(ke, a.ke_part, i, a.n);
@@ -538,10 +539,17 @@ __global__ void __launch_bounds__(kThreads) k_finish(StepArgs<T> a)
 
 // one block: KE of the body, KE_max, step counters, relax test
 __global__ void __launch_bounds__(kThreads) k_ke_final(const double* __restrict__ part, int np,
-                                                        DevScalars* sc, int damped)
+                                                        DevScalars* sc, int damped, const int* dflag)
 {
     if (sc->done) return;
-    ke_finalize(part, np, sc, damped);
+    ke_finalize(part, np, sc, dflag ? *dflag : damped);
+}
+
+// the random choice of the step (Eq. viscosity-reset) on the device, for
+// replayed multi-step graphs: the same Philox draw as the host's
+__global__ void k_decide_one(const DevScalars* sc, unsigned long long seed, double alpha, int* dflag)
+{
+    *dflag = !sc->done && random_phi(seed, (unsigned long long)sc->step) < alpha;
 }
 
 

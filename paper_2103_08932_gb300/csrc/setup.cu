@@ -79,17 +79,32 @@ __global__ void k_bbox_partial(const double* __restrict__ r0aos, int n, double* 
 
 __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ out)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double smin[3][kThreads], smax[3][kThreads];
+    const int t = threadIdx.x;
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nb; ++b)
+    for (int b = t; b < nb; b += blockDim.x)
         for (int a = 0; a < 3; ++a) {
             mn[a] = fmin(mn[a], part[b * 6 + a]);
             mx[a] = fmax(mx[a], part[b * 6 + 3 + a]);
         }
     for (int a = 0; a < 3; ++a) {
-        out[a] = mn[a];
-        out[3 + a] = mx[a];
+        smin[a][t] = mn[a];
+        smax[a][t] = mx[a];
     }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][t] = fmin(smin[a][t], smin[a][t + s]);
+                smax[a][t] = fmax(smax[a][t], smax[a][t + s]);
+            }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int a = 0; a < 3; ++a) {
+            out[a] = smin[a][0];
+            out[3 + a] = smax[a][0];
+        }
 }
 
 // ------------------------------------------------------------------ cells
@@ -407,8 +422,43 @@ __global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx
     });
     // Canonical neighbour order of a row: ascending ORIGINAL particle id.  The
     // pairwise local operator applies its pair updates in row order (Sec. 3.2),
-    // so the order is part of the result; insertion sort by perm[col].
-    {
+    // so the order is part of the result; insertion sort by perm[col], on a
+    // thread-local copy of the row when it fits (keys read once), else in place.
+    constexpr int kSortCap = 160;
+    if (k - row_ptr[i] <= kSortCap) {
+        const int k0 = row_ptr[i], deg = k - k0;
+        int key[kSortCap], cj[kSortCap];
+        uint16_t lj[kSortCap];
+        T wj[kSortCap];
+        for (int a = 0; a < deg; ++a) {
+            cj[a] = col[k0 + a];
+            lj[a] = loc[k0 + a];
+            wj[a] = w[k0 + a];
+            key[a] = perm[cj[a]];
+        }
+        for (int a = 1; a < deg; ++a) {
+            const int kk = key[a], cc = cj[a];
+            const uint16_t ll = lj[a];
+            const T ww = wj[a];
+            int m = a - 1;
+            while (m >= 0 && key[m] > kk) {
+                key[m + 1] = key[m];
+                cj[m + 1] = cj[m];
+                lj[m + 1] = lj[m];
+                wj[m + 1] = wj[m];
+                --m;
+            }
+            key[m + 1] = kk;
+            cj[m + 1] = cc;
+            lj[m + 1] = ll;
+            wj[m + 1] = ww;
+        }
+        for (int a = 0; a < deg; ++a) {
+            col[k0 + a] = cj[a];
+            loc[k0 + a] = lj[a];
+            w[k0 + a] = wj[a];
+        }
+    } else {
         const int k0 = row_ptr[i];
         for (int a = k0 + 1; a < k; ++a) {
             int cj = col[a];
@@ -566,7 +616,7 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_TRY(dalloc(b, &bpart, (size_t)nbb * 6));
     SRDR_TRY(dalloc(b, &bbox, 6));
     k_bbox_partial<<<nbb, kThreads, 0, st>>>(r0aos, n, bpart);
-    k_bbox_final<<<1, 32, 0, st>>>(bpart, nbb, bbox);
+    k_bbox_final<<<1, kThreads, 0, st>>>(bpart, nbb, bbox);
     double hb[6];
     SRDR_CK(cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st));
     SRDR_CK(cudaStreamSynchronize(st));

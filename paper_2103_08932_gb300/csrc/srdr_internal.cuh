@@ -93,6 +93,7 @@ struct StepArgs {
     const T* __restrict__ Gs;   // [3][n]
     const T* __restrict__ dvisc; // [n][4] explicit comparator: dt a_visc(v^n), else null
     const T* __restrict__ bf;    // [n][4] per-particle body force (twist), else null
+    const int* dflag;            // device-decided damping of this step (graph replay), else null
     T* __restrict__ v;          // [n][4] (vx, vy, vz, 1/m)
     double* __restrict__ u;     // [3][n] FP64 mode
     float* __restrict__ uhi;    // [n][4] FP32 mode, u = hi + lo
@@ -123,6 +124,7 @@ struct SweepArgs {
     const T* __restrict__ srd;   // [n] 1 / ((sum_j B_j - m_i)^2 + sum_j B_j^2)
     T* __restrict__ v;
     DevScalars* sc;
+    const int* dflag;  // device-decided damping of this step (graph replay), else null
     T c;          // 2 eta~ dt_loc, so that B_j = c w_ij
     int backward;
     int pairwise;
@@ -216,6 +218,12 @@ struct srdr_body {
 
     // kernel-class timing (CUDA events on the body stream)
     int profiling = 0;
+    // replay of captured multi-step graphs (small bodies, damping decided on
+    // the device): the flag word, the graph, its step count, availability
+    int* dflag_d = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graphs_ok = 1;
+    int64_t graph_launches[SRDR_K_NCLASS] = {0, 0, 0, 0, 0};  // kernels per graph replay
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
     size_t ev_next = 0;

@@ -23,6 +23,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kUnroll = 8;  // sliced-ELL slots per batch of loads in the passes
+constexpr int kGraphSteps = 32;       // steps per captured graph (small bodies)
+constexpr int64_t kGraphMaxN = 65536;  // bodies up to this size replay graphs
 inline int nblocks(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
 #include "passes.cuh"
@@ -252,50 +254,114 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         b->k_launch[k] += nlaunch;
         b->launches += nlaunch;
     };
-    for (int64_t s = 0; s < nsteps; ++s) {
-        const uint64_t step = (uint64_t)(b->step + s);
-        const bool damp = damping && random_phi(b->desc.seed, step) < b->desc.alpha;
+    // device-decided copies of the arguments (multi-step graph replay)
+    StepArgs<T> ad = a;
+    SweepArgs<T> swd = sw;
+    void* sweep_params_d[] = {&swd, &cptr, &ncol, &bar};
+
+    // One step on stream q.  dev: the random choice is drawn on the device
+    // (k_decide_one) and every kernel of the step reads it, so the launch
+    // sequence is the same for every step; otherwise the host draws it and
+    // launches only what the step needs.  Both give the same bits.
+    auto one_step = [&](cudaStream_t q, bool dev, bool damp) -> srdr_status {
+        const StepArgs<T>& A = dev ? ad : a;
+        if (dev && damping)
+            k_decide_one<<<1, 1, 0, q>>>(b->sc, (unsigned long long)b->desc.seed, b->desc.alpha, b->dflag_d);
         prof_begin(b, SRDR_K_PASS_A, &ev);
         if (tiled)
-            k_pass_a_tiled<T, D, MAT><<<b->nbricks, kTileThreads, smem_a, st>>>(a, tl);
+            k_pass_a_tiled<T, D, MAT><<<b->nbricks, kTileThreads, smem_a, q>>>(A, tl);
         else
-            k_pass_a<T, D, MAT><<<nb, kThreads, 0, st>>>(a);
+            k_pass_a<T, D, MAT><<<nb, kThreads, 0, q>>>(A);
         prof_end(b, SRDR_K_PASS_A, ev);
         counted(SRDR_K_PASS_A, 1);
         if (explicit_visc) {
             // the explicit comparator's damping, at v^n, before the force pass
             prof_begin(b, SRDR_K_SWEEP, &ev);
-            k_visc<T, D><<<nb, kThreads, 0, st>>>((int)b->n, b->row_ptr, b->col,
-                                                  static_cast<const T*>(b->w), static_cast<const T*>(b->v),
-                                                  static_cast<const T*>(b->mass), c2eta_dt,
-                                                  static_cast<T*>(b->dvisc), b->sc);
+            k_visc<T, D><<<nb, kThreads, 0, q>>>((int)b->n, b->row_ptr, b->col,
+                                                 static_cast<const T*>(b->w), static_cast<const T*>(b->v),
+                                                 static_cast<const T*>(b->mass), c2eta_dt,
+                                                 static_cast<T*>(b->dvisc), b->sc);
             prof_end(b, SRDR_K_SWEEP, ev);
             counted(SRDR_K_SWEEP, 1);
         }
         prof_begin(b, SRDR_K_PASS_B, &ev);
         if (tiled)
-            k_pass_b_tiled<T, D><<<b->nbricks, kTileThreads, smem_b, st>>>(a, tl, damp ? 0 : 1);
+            k_pass_b_tiled<T, D><<<b->nbricks, kTileThreads, smem_b, q>>>(A, tl, damp ? 0 : 1);
         else
-            k_pass_b<T, D><<<nb, kThreads, 0, st>>>(a, damp ? 0 : 1);
+            k_pass_b<T, D><<<nb, kThreads, 0, q>>>(A, damp ? 0 : 1);
         prof_end(b, SRDR_K_PASS_B, ev);
         counted(SRDR_K_PASS_B, 1);
-        if (damp) {
+        if (dev ? damping : damp) {
             prof_begin(b, SRDR_K_SWEEP, &ev);
-            const int nl = 1;
             SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(grid), dim3(sl.threads),
-                                                sweep_params, smem, st));
+                                                dev ? sweep_params_d : sweep_params, smem, q));
             prof_end(b, SRDR_K_SWEEP, ev);
-            counted(SRDR_K_SWEEP, nl);
+            counted(SRDR_K_SWEEP, 1);
             prof_begin(b, SRDR_K_FINISH, &ev);
-            k_finish<T><<<nb, kThreads, 0, st>>>(a);
+            k_finish<T><<<nb, kThreads, 0, q>>>(A);
             prof_end(b, SRDR_K_FINISH, ev);
             counted(SRDR_K_FINISH, 1);
         }
         prof_begin(b, SRDR_K_KE, &ev);
-        if (tiled && !damp) k_ke_slices<<<nb, kThreads, 0, st>>>(b->ke_pp, (int)b->n, b->ke_part, b->sc);
-        k_ke_final<<<1, kThreads, 0, st>>>(b->ke_part, b->nslices, b->sc, damp ? 1 : 0);
+        const bool slices = tiled && (dev || !damp);
+        if (slices)
+            k_ke_slices<<<nb, kThreads, 0, q>>>(b->ke_pp, (int)b->n, b->ke_part, b->sc, A.dflag);
+        k_ke_final<<<1, kThreads, 0, q>>>(b->ke_part, b->nslices, b->sc, damp ? 1 : 0, A.dflag);
         prof_end(b, SRDR_K_KE, ev);
-        counted(SRDR_K_KE, tiled && !damp ? 2 : 1);
+        counted(SRDR_K_KE, slices ? 2 : 1);
+        return SRDR_OK;
+    };
+
+    int64_t s0 = 0;
+    // small bodies: replay a captured graph of kGraphSteps device-decided
+    // steps (their steps are short enough for launch overhead to dominate)
+    if (!b->profiling && b->graphs_ok && b->n <= kGraphMaxN && nsteps >= kGraphSteps) {
+        if (!b->dflag_d) {
+            SRDR_TRY(dalloc(b, &b->dflag_d, 1));
+            SRDR_CK(cudaMemsetAsync(b->dflag_d, 0, sizeof(int), st));
+        }
+        ad.dflag = b->dflag_d;
+        swd.dflag = b->dflag_d;
+        if (!b->graph) {
+            // captured on a private stream (the body's may be the legacy
+            // default stream, which cannot be captured); launches are not
+            // counted while capturing
+            cudaStream_t cs = nullptr;
+            cudaGraph_t g = nullptr;
+            const int64_t l0 = b->launches;
+            int64_t k0[SRDR_K_NCLASS];
+            for (int k = 0; k < SRDR_K_NCLASS; ++k) k0[k] = b->k_launch[k];
+            bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                for (int k = 0; k < kGraphSteps && ok; ++k) ok = one_step(cs, true, false) == SRDR_OK;
+                ok = (cudaStreamEndCapture(cs, &g) == cudaSuccess) && ok && g &&
+                     cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess;
+            }
+            if (g) cudaGraphDestroy(g);
+            if (cs) cudaStreamDestroy(cs);
+            cudaGetLastError();
+            b->launches = l0;
+            for (int k = 0; k < SRDR_K_NCLASS; ++k) b->graph_launches[k] = b->k_launch[k] - k0[k];
+            for (int k = 0; k < SRDR_K_NCLASS; ++k) b->k_launch[k] = k0[k];
+            if (!ok) {
+                b->graph = nullptr;
+                b->graphs_ok = 0;
+            }
+        }
+        if (b->graph) {
+            const int64_t ng = nsteps / kGraphSteps;
+            for (int64_t g = 0; g < ng; ++g) {
+                SRDR_CK(cudaGraphLaunch(b->graph, st));
+                for (int k = 0; k < SRDR_K_NCLASS; ++k) counted(k, (int)b->graph_launches[k]);
+            }
+            s0 = ng * kGraphSteps;
+        }
+    }
+    for (int64_t s = s0; s < nsteps; ++s) {
+        const uint64_t step = (uint64_t)(b->step + s);
+        const bool damp = damping && random_phi(b->desc.seed, step) < b->desc.alpha;
+        SRDR_TRY(one_step(st, false, damp));
     }
     SRDR_CK(cudaGetLastError());
     b->step += nsteps;

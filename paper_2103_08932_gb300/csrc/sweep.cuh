@@ -510,6 +510,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
 {
     constexpr int L = 32 / G;
     if (*(volatile int*)&a.sc->done) return;
+    if (a.dflag && *a.dflag == 0) return;  // every block reads the same word: no barrier is left waiting
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / L, gl = lane % L;

@@ -176,6 +176,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kTileThreads) k_pass_b_tiled(StepArgs<T> a, TileArgs<T> tl, int final_step)
 {
     if (a.sc->done) return;
+    if (a.dflag) final_step = *a.dflag == 0;
     extern __shared__ __align__(16) unsigned char tsm[];
     const BrickInfo bi = tl.info[blockIdx.x];
     stage_halo_pb(tsm, reinterpret_cast<const unsigned char*>(a.PB), a.n, tl.halo + bi.halo_base, bi.nhalo,
@@ -225,9 +226,10 @@ __global__ void __launch_bounds__(kTileThreads) k_pass_b_tiled(StepArgs<T> a, Ti
 // final force pass: the warp sums of slice_partial_store, so the body's KE
 // has the same bits as with the sliced-ELL force pass
 __global__ void __launch_bounds__(kThreads) k_ke_slices(const double* __restrict__ ke_pp, int n,
-                                                         double* __restrict__ part, const DevScalars* sc)
+                                                         double* __restrict__ part, const DevScalars* sc,
+                                                         const int* dflag)
 {
-    if (sc->done) return;
+    if (sc->done || (dflag && *dflag)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     slice_partial_store(i < n ? ke_pp[i] : 0.0, part, i, n);
 }
