@@ -1,5 +1,33 @@
 #include "pairg.cuh"
 
+// Loads of the neighbour streams (read once per pass): not allocated in L1,
+// which then holds the neighbours' gathered records (measured 6 % faster
+// passes on GB300)
+__device__ inline int ld_stream(const int* p)
+{
+    int r;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+__device__ inline float ld_stream(const float* p)
+{
+    float r;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(r) : "l"(p));
+    return r;
+}
+__device__ inline double ld_stream(const double* p)
+{
+    double r;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(r) : "l"(p));
+    return r;
+}
+__device__ inline uint16_t ld_stream(const uint16_t* p)
+{
+    unsigned short r;
+    asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(r) : "l"(p));
+    return r;
+}
+
 // ------------------------------------------------------------------ layouts
 // u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 hi and lo arrays
 // [n][4] each (u = hi + lo).
@@ -287,10 +315,10 @@ __device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
         for (int u = 0; u < kUnroll; ++u) {
             const int k = base + (t0 + u) * 32 + lane;
             const bool in = t0 + u < width;
-            jj[u] = in ? __ldg(a.sell_col + k) : i;
-            gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
-            gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
-            if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
+            jj[u] = in ? ld_stream(a.sell_col + k) : i;
+            gg[u][0] = in ? ld_stream(a.g0 + k) : T(0);
+            gg[u][1] = in ? ld_stream(a.g1 + k) : T(0);
+            if constexpr (D == 3) gg[u][2] = in ? ld_stream(a.g2 + k) : T(0);
         }
         T xj[kUnroll][3], lj[kUnroll][3];
 #pragma unroll
@@ -482,10 +510,10 @@ __device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_
         for (int u = 0; u < kUnroll; ++u) {
             const int k = base + (t0 + u) * 32 + lane;
             const bool in = t0 + u < width;
-            jj[u] = in ? __ldg(a.sell_col + k) : i;
-            gg[u][0] = in ? __ldg(a.g0 + k) : T(0);
-            gg[u][1] = in ? __ldg(a.g1 + k) : T(0);
-            if constexpr (D == 3) gg[u][2] = in ? __ldg(a.g2 + k) : T(0);
+            jj[u] = in ? ld_stream(a.sell_col + k) : i;
+            gg[u][0] = in ? ld_stream(a.g0 + k) : T(0);
+            gg[u][1] = in ? ld_stream(a.g1 + k) : T(0);
+            if constexpr (D == 3) gg[u][2] = in ? ld_stream(a.g2 + k) : T(0);
         }
         T Pj[kUnroll][D][D];
 #pragma unroll

@@ -157,10 +157,10 @@ __global__ void __launch_bounds__(kTileThreads) k_pass_a_tiled(StepArgs<T> a, Ti
             for (int u = 0; u < kTileUnroll; ++u) {
                 const int kk = base + (t0 + u) * 32 + lane;
                 const bool in = t0 + u < width;
-                ll[u] = in ? (int)__ldg(tl.lidx + kk) : hi;
-                gg[u][0] = in ? __ldg(tl.g0 + kk) : T(0);
-                gg[u][1] = in ? __ldg(tl.g1 + kk) : T(0);
-                if constexpr (D == 3) gg[u][2] = in ? __ldg(tl.g2 + kk) : T(0);
+                ll[u] = in ? (int)ld_stream(tl.lidx + kk) : hi;
+                gg[u][0] = in ? ld_stream(tl.g0 + kk) : T(0);
+                gg[u][1] = in ? ld_stream(tl.g1 + kk) : T(0);
+                if constexpr (D == 3) gg[u][2] = in ? ld_stream(tl.g2 + kk) : T(0);
             }
             T xj[kTileUnroll][3], lj[kTileUnroll][3];
 #pragma unroll
@@ -203,10 +203,10 @@ __global__ void __launch_bounds__(kTileThreads) k_pass_b_tiled(StepArgs<T> a, Ti
             for (int u = 0; u < kTileUnroll; ++u) {
                 const int kk = base + (t0 + u) * 32 + lane;
                 const bool in = t0 + u < width;
-                ll[u] = in ? (int)__ldg(tl.lidx + kk) : hi;
-                gg[u][0] = in ? __ldg(tl.g0 + kk) : T(0);
-                gg[u][1] = in ? __ldg(tl.g1 + kk) : T(0);
-                if constexpr (D == 3) gg[u][2] = in ? __ldg(tl.g2 + kk) : T(0);
+                ll[u] = in ? (int)ld_stream(tl.lidx + kk) : hi;
+                gg[u][0] = in ? ld_stream(tl.g0 + kk) : T(0);
+                gg[u][1] = in ? ld_stream(tl.g1 + kk) : T(0);
+                if constexpr (D == 3) gg[u][2] = in ? ld_stream(tl.g2 + kk) : T(0);
             }
             T Pj[kTileUnroll][D][D];
 #pragma unroll
