@@ -112,7 +112,7 @@ __global__ void k_batch_finish(const BatchEntry<T>* __restrict__ tab, const int2
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_batch_ke(const BatchEntry<T>* __restrict__ tab,
+__global__ void __launch_bounds__(kKeThreads) k_batch_ke(const BatchEntry<T>* __restrict__ tab,
                                                         const int* __restrict__ bodies,
                                                         const int* __restrict__ damp)
 {
@@ -463,7 +463,7 @@ srdr_status enqueue_steps(srdr_batch* bt, int64_t nsteps, const void* sweep_fn)
         SRDR_CK(cudaLaunchCooperativeKernel(sweep_fn, dim3(bt->sweep_grid), dim3(32), sweep_params,
                                             bt->sweep_smem, bt->stream));
         k_batch_finish<T><<<pblocks, tpb, 0, bt->stream>>>(tab, items, nitems);
-        k_batch_ke<T><<<bt->nactive, kThreads, 0, bt->stream>>>(tab, bt->active_d, bt->damp);
+        k_batch_ke<T><<<bt->nactive, kKeThreads, 0, bt->stream>>>(tab, bt->active_d, bt->damp);
         bt->launches += 6;
     }
     SRDR_CK(cudaGetLastError());

@@ -358,10 +358,14 @@ __device__ inline void slice_partial_store(double x, double* out, int i, int n)
 
 // One block of kThreads: FP64 KE of one body from its slice partials in a
 // fixed order, its running maximum, the step counters and the relax test.
+// threads of the one-block kinetic-energy reductions (single body and batch
+// use the same count, so a body's KE has the same bits in both)
+constexpr int kKeThreads = 256;
+
 __device__ inline void ke_finalize(const double* __restrict__ part, int np, DevScalars* sc,
                                    int damped)
 {
-    __shared__ double s[kThreads / 32];
+    __shared__ double s[kKeThreads / 32];
     double x = 0.0;
     // loads issued 16 at a time, added in index order (part[t], part[t + B], ...)
     for (int b0 = threadIdx.x; b0 < np; b0 += 16 * blockDim.x) {
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(StepArgs<T> a)
 }
 
 // one block: KE of the body, KE_max, step counters, relax test
-__global__ void __launch_bounds__(kThreads) k_ke_final(const double* __restrict__ part, int np,
+__global__ void __launch_bounds__(kKeThreads) k_ke_final(const double* __restrict__ part, int np,
                                                         DevScalars* sc, int damped, const int* dflag)
 {
     if (sc->done) return;

@@ -306,7 +306,7 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         const bool slices = tiled && (dev || !damp);
         if (slices)
             k_ke_slices<<<nb, kThreads, 0, q>>>(b->ke_pp, (int)b->n, b->ke_part, b->sc, A.dflag);
-        k_ke_final<<<1, kThreads, 0, q>>>(b->ke_part, b->nslices, b->sc, damp ? 1 : 0, A.dflag);
+        k_ke_final<<<1, kKeThreads, 0, q>>>(b->ke_part, b->nslices, b->sc, damp ? 1 : 0, A.dflag);
         prof_end(b, SRDR_K_KE, ev);
         counted(SRDR_K_KE, slices ? 2 : 1);
         return SRDR_OK;
