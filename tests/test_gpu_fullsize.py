@@ -1,0 +1,98 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch
+configuration bench.py times (FP32-mixed, autotuned sweep, sliced-ELL
+passes).
+
+* 3D plate (406,000 particles): from a state the GPU reached after 200 steps,
+  eight steps (a damped one included) of the GPU and of the FP64 oracle
+  started from that same state agree within the FP32-mixed tolerance.
+* 3D compression block (2.05 M particles): FP32-mixed against all-FP64 GPU
+  after 20 steps (the FP64 path is oracle-exact at smaller sizes).
+* 256 uneven bodies (10.4 M particles): sampled bodies of the batch equal the
+  same bodies stepped alone, bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2103_08932_gb300 import srdr
+from paper_2103_08932_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2103_08932_gb300 import build
+    build.build()
+    srdr.lib()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def test_full_plate_steps_from_a_gpu_state_match_oracle():
+    spec = S.cantilever_plate_3d()
+    run = srdr.Body(srdr.make_desc(spec, precision=srdr.SRDR_FP32_MIXED))
+    run.step(200)
+    u, v = run.displacement(), run.velocity()
+    run.close()
+    gb = srdr.Body(srdr.make_desc(spec, precision=srdr.SRDR_FP32_MIXED))
+    gb.write_state(u, v, step_index=0)
+    r0, flags, _ = S.lattice(spec)
+    p = O.Params(dim=3, material=spec.material, rho0=spec.rho0, E=spec.E, nu=spec.nu, h=spec.h,
+                 gravity=spec.gravity, beta=spec.beta, L_char=spec.L_char, alpha=spec.alpha,
+                 seed=spec.seed, f_form=O.F_DISPLACEMENT)
+    ob = O.OracleBody(p, r0, vol_default=spec.vol, flags=flags)
+    ob.set(O.U, u)
+    ob.set(O.V, v)
+    assert gb.stats()["dt"] == pytest.approx(ob.dt, rel=1e-14)
+    worst_v = worst_u = 0.0
+    for _ in range(8):  # seed 1 damps step 7
+        gb.step(1)
+        ob.step(1)
+        worst_v = max(worst_v, rel(gb.velocity(), ob.v))
+        worst_u = max(worst_u, rel(gb.displacement(), ob.u))
+    assert gb.stats()["damped_steps"] == ob.damped_steps == 1
+    assert worst_v <= 2e-5
+    assert worst_u <= 1e-6
+
+
+def test_full_block_fp32_mixed_against_fp64():
+    spec = S.compression_block_3d()
+    us = {}
+    for prec in (srdr.SRDR_FP32_MIXED, srdr.SRDR_FP64):
+        b = srdr.Body(srdr.make_desc(spec, precision=prec))
+        assert b.n == 2046875
+        b.step(20)
+        us[prec] = b.displacement()
+        b.close()
+    moved = us[srdr.SRDR_FP64] - S.lattice(spec)[2]
+    d = np.abs(us[srdr.SRDR_FP32_MIXED] - us[srdr.SRDR_FP64]).max()
+    assert d <= 1e-5 * np.abs(us[srdr.SRDR_FP64]).max()
+    assert d <= 1e-4 * np.abs(moved).max()
+
+
+def test_full_batch_sampled_bodies_equal_alone():
+    specs = S.random_bodies(256, 1e3, 2e5, 3)
+    bodies = [srdr.Body(srdr.make_desc(s, precision=srdr.SRDR_FP32_MIXED)) for s in specs]
+    total = sum(b.n for b in bodies)
+    assert total > 1e7
+    batch = srdr.Batch(bodies)
+    batch.step(12)
+    sizes = np.array([b.n for b in bodies])
+    rng = np.random.default_rng(0)
+    sample = list(np.argsort(sizes)[-3:]) + list(np.argsort(sizes)[:2]) + list(rng.choice(256, 3, replace=False))
+    for k in sample:
+        alone = srdr.Body(srdr.make_desc(specs[k], precision=srdr.SRDR_FP32_MIXED))
+        alone.step(12)
+        assert np.array_equal(alone.velocity(), bodies[k].velocity()), k
+        assert np.array_equal(alone.displacement(), bodies[k].displacement()), k
+        assert alone.stats()["ke"] == bodies[k].stats()["ke"], k
+        alone.close()
+    batch.close()
+    for b in bodies:
+        b.close()
