@@ -310,7 +310,6 @@ SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
     s.nz = b->nc[2];
     s.cell_start = b->cell_start;
     s.colour_cells = b->colour_cells;
-    s.ncells_colour = b->ncells_nonempty;
     s.row_ptr = b->row_ptr;
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);

@@ -115,7 +115,6 @@ struct SweepArgs {
     int nx, ny, nz;
     const int* __restrict__ cell_start;
     const int* __restrict__ colour_cells;  // cells of this colour
-    int ncells_colour;
     const int* __restrict__ row_ptr;
     const uint16_t* __restrict__ loc;
     const T* __restrict__ w;
@@ -126,7 +125,6 @@ struct SweepArgs {
     DevScalars* sc;
     const int* dflag;  // device-decided damping of this step (graph replay), else null
     T c;          // 2 eta~ dt_loc, so that B_j = c w_ij
-    int backward;
     int pairwise;
     int max_foot;
     int max_pairs;

@@ -60,7 +60,6 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     s.nz = b->nc[2];
     s.cell_start = b->cell_start;
     s.colour_cells = b->colour_cells;  // all colours; colour_ptr_d indexes into it
-    s.ncells_colour = b->ncells_nonempty;
     s.row_ptr = b->row_ptr;
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);

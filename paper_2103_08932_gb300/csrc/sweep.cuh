@@ -453,15 +453,6 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
     __syncwarp(gmask);
 }
 
-// Both stages back to back.
-template <typename T, int D, int L>
-__device__ inline void sweep_cell(const SweepArgs<T>& a, int c, int mode, const CellSmem<T, D>& s,
-                                  int gl, unsigned gmask)
-{
-    const CellStage st = stage_cell<T, D, L>(a, c, s, gl, gmask);
-    run_cell<T, D, L>(a, st, mode, s, gl, gmask);
-}
-
 // Colour of phase ph (forward colours 0..nc-1, then backward nc-1..0).
 __device__ inline int phase_colour(int ph, int ncolours) { return ph >= ncolours ? 2 * ncolours - 1 - ph : ph; }
 
