@@ -184,10 +184,15 @@ srdr_status srdr_body_read_field(const srdr_body* body, int field, double* host_
                                  size_t n_doubles);
 
 /* Kernel timing with CUDA events recorded on the body's stream around each
- * kernel class of every step (the damping sweep class spans all colour
- * launches of one damped step).  srdr_body_profile(body, 1) clears and starts
- * recording, (body, 0) stops; srdr_body_kernel_times synchronises and returns
- * the accumulated device milliseconds and launch counts per class. */
+ * kernel class of the timed steps (the damping sweep class spans the whole
+ * S_d of a damped step).  srdr_body_profile(body, k) with k > 0 clears the
+ * records and times every k-th step (steps whose index is a multiple of k:
+ * k = 1 times all of them; a larger k keeps the events' own cost out of most
+ * steps, and the random choice makes the sample of damped steps unbiased);
+ * k = 0 stops.  srdr_body_kernel_times synchronises and returns the
+ * accumulated device milliseconds and timed intervals per class and the
+ * launches of all steps since the profile call.  Profiled stepping launches
+ * every step directly (no graph replay). */
 enum { SRDR_K_PASS_A = 0, SRDR_K_PASS_B = 1, SRDR_K_SWEEP = 2, SRDR_K_FINISH = 3, SRDR_K_KE = 4,
        SRDR_K_NCLASS = 5 };
 typedef struct {
@@ -199,7 +204,7 @@ srdr_status srdr_body_profile(srdr_body* body, int enable);
 
 /* Kernel mapping of the damping sweep: sweep_cells_per_warp = 1, 2 or 4 cells
  * per warp and sweep_warps_per_block = 1 or 4, or both 0 to let the
- * autotuner time the six mappings on the body's first damped step (the
+ * autotuner time G = 1, 2 with W = 1, 4 on the body's first damped step (the
  * default).  The choice changes speed only: the sweep's sums follow one fixed
  * order, so results are bitwise the same. */
 srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp, int sweep_warps_per_block);

@@ -51,7 +51,7 @@ void prof_begin(srdr_body* b, int k, cudaEvent_t* ev)
 {
     (void)k;
     *ev = nullptr;
-    if (!b->profiling) return;
+    if (!b->prof_active) return;
     if (b->ev_next >= b->ev_pool.size()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -63,7 +63,7 @@ void prof_begin(srdr_body* b, int k, cudaEvent_t* ev)
 
 void prof_end(srdr_body* b, int k, cudaEvent_t ev)
 {
-    if (!b->profiling || !ev) return;
+    if (!b->prof_active || !ev) return;
     if (b->ev_next >= b->ev_pool.size()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -630,7 +630,7 @@ srdr_status srdr_body_profile(srdr_body* b, int enable)
         b->ev_next = 0;
         for (int k = 0; k < SRDR_K_NCLASS; ++k) b->k_launch[k] = 0;
     }
-    b->profiling = enable ? 1 : 0;
+    b->profiling = enable > 0 ? enable : 0;
     return SRDR_OK;
 }
 

@@ -215,7 +215,8 @@ struct srdr_body {
     int64_t launches = 0;
 
     // kernel-class timing (CUDA events on the body stream)
-    int profiling = 0;
+    int profiling = 0;               // 0 off, k > 0: time every k-th step
+    int prof_active = 0;             // the step being enqueued is timed
     // replay of captured multi-step graphs (small bodies, damping decided on
     // the device): the flag word, the graph, its step count, availability
     int* dflag_d = nullptr;

@@ -131,9 +131,11 @@ srdr_status sweep_launch(srdr_body* b, SweepLaunch<T, D>* out)
     }
 }
 
-// Autotuner of the sweep's mapping: time G = 1, 2, 4 cells per warp with
-// W = 1 or 4 warps per block on a scratch copy of v (the sweep writes v, the
-// body's state must not change) and keep the fastest.  The sweep's
+// Autotuner of the sweep's mapping: time G = 1 or 2 cells per warp with
+// W = 1 or 4 warps per block (one warm-up and one timed launch each) on a
+// scratch copy of v (the sweep writes v, the body's state must not change)
+// and keep the fastest.  G = 4 (measured slower on every body tried) stays
+// available through srdr_body_tune.  The sweep's
 // arithmetic does not depend on the mapping (its reductions follow one
 // 32-lane order), so the choice changes speed, never results.
 template <typename T, int D>
@@ -155,7 +157,7 @@ srdr_status autotune_sweep(srdr_body* b)
     SRDR_CK(cudaEventCreate(&e1));
     float best = 3.0e38f;
     int best_g = b->sweep_cells_per_warp, best_w = b->sweep_warps_per_block;
-    for (int g : {1, 2, 4})
+    for (int g : {1, 2})
         for (int w : {1, 4}) {
             b->sweep_cells_per_warp = g;
             b->sweep_warps_per_block = w;
@@ -164,9 +166,8 @@ srdr_status autotune_sweep(srdr_body* b)
             SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params, sl.smem,
                                                 b->stream));
             SRDR_CK(cudaEventRecord(e0, b->stream));
-            for (int r = 0; r < 2; ++r)
-                SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params,
-                                                    sl.smem, b->stream));
+            SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params, sl.smem,
+                                                b->stream));
             SRDR_CK(cudaEventRecord(e1, b->stream));
             SRDR_CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -360,7 +361,10 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
     for (int64_t s = s0; s < nsteps; ++s) {
         const uint64_t step = (uint64_t)(b->step + s);
         const bool damp = damping && random_phi(b->desc.seed, step) < b->desc.alpha;
-        SRDR_TRY(one_step(st, false, damp));
+        b->prof_active = b->profiling > 0 && step % (uint64_t)b->profiling == 0;
+        const srdr_status r = one_step(st, false, damp);
+        b->prof_active = 0;
+        SRDR_TRY(r);
     }
     SRDR_CK(cudaGetLastError());
     b->step += nsteps;

@@ -280,7 +280,9 @@ class Body:
         _check(lib().srdr_body_pass_mapping(self.h, int(mapping), bx, by, bz))
 
     def profile(self, enable=True):
-        _check(lib().srdr_body_profile(self.h, 1 if enable else 0))
+        """True / k > 0: time every (k-th) step's kernels with CUDA events; False / 0: stop."""
+        k = (1 if enable else 0) if isinstance(enable, bool) else int(enable)
+        _check(lib().srdr_body_profile(self.h, k))
 
     def kernel_times(self):
         t = srdr_kernel_times()
