@@ -45,6 +45,26 @@ __device__ inline double dist2(int dim, const double* r0, int n, int i, int j)
     return s;
 }
 
+// Neighbour test 0 < |r0_i - r0_j|^2 < rc2, decided exactly by the FP64
+// operations above; an FP32 estimate from the cell offsets and packed cells
+// (error below 1e-6 rc2 for any body size) settles the clear cases first, so
+// FP64 work is spent only near the cut-off and on the pairs that are kept.
+// Returns 1 clearly inside, 0 clearly outside, -1 undecided.
+__device__ inline int near_prefilter(int dim, const float4& oi, int ci, const float4& oj, int cj, float rcf,
+                                     float rc2f)
+{
+    const float dx = fmaf((float)cell_diff<0>(ci, cj), rcf, oi.x - oj.x);
+    const float dy = fmaf((float)cell_diff<10>(ci, cj), rcf, oi.y - oj.y);
+    float d2 = dx * dx + dy * dy;
+    if (dim == 3) {
+        const float dz = fmaf((float)cell_diff<20>(ci, cj), rcf, oi.z - oj.z);
+        d2 += dz * dz;
+    }
+    if (d2 > rc2f * 1.00001f) return 0;
+    if (d2 < rc2f * 0.99999f && d2 > rc2f * 1e-5f) return 1;
+    return -1;
+}
+
 // ------------------------------------------------------------------ bbox
 __global__ void k_bbox_partial(const double* __restrict__ r0aos, int n, double* __restrict__ part)
 {
@@ -114,6 +134,22 @@ struct Grid {
     double lo0, lo1, lo2;
     double rc;
 };
+
+// FP32 cell offsets (for the prefilter) and packed cell coordinates
+__global__ void k_cell_pos_f(const double* __restrict__ r0, int n, Grid g, const int* __restrict__ cell_of,
+                             float4* __restrict__ of, int* __restrict__ ccell)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cell_of[i];
+    const int cc[3] = {c % g.nx, (c / g.nx) % g.ny, c / (g.nx * g.ny)};
+    const double lo[3] = {g.lo0, g.lo1, g.lo2};
+    float o[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < g.dim; ++a) o[a] = (float)fma(-(double)cc[a], g.rc, r0[(size_t)a * n + i] - lo[a]);
+    of[i] = make_float4(o[0], o[1], o[2], 0.f);
+    ccell[i] = pack_cell(c, g.nx, g.ny);
+}
+
 
 __device__ inline int cell_coord(double x, double lo, double rc, int ncell)
 {
@@ -366,14 +402,23 @@ __device__ inline int for_footprint(int c, int dim, int nx, int ny, int nz,
 
 __global__ void k_csr_count(const double* __restrict__ r0, int n, int dim, int nx, int ny, int nz,
                             const int* __restrict__ start, const int* __restrict__ cell_of,
-                            double rc2, int* __restrict__ deg)
+                            const float4* __restrict__ of, const int* __restrict__ ccell, float rcf,
+                            float rc2f, double rc2, int* __restrict__ deg)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int cnt = 0;
+    const float4 oi = of[i];
+    const int ci = ccell[i];
     for_footprint(cell_of[i], dim, nx, ny, nz, start, [&](int a, int b, int) {
         for (int j = a; j < b; ++j) {
             if (j == i) continue;
+            const int pre = near_prefilter(dim, oi, ci, of[j], ccell[j], rcf, rc2f);
+            if (pre == 0) continue;
+            if (pre == 1) {
+                ++cnt;
+                continue;
+            }
             double d2 = dist2(dim, r0, n, i, j);
             if (d2 > 0.0 && d2 < rc2) ++cnt;
         }
@@ -391,7 +436,8 @@ __global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx
                            const int* __restrict__ row_ptr, int* __restrict__ col,
                            uint16_t* __restrict__ loc, T* __restrict__ w, T* __restrict__ sumw,
                            T* __restrict__ sumw2, T* __restrict__ B0,
-                           const int* __restrict__ perm, DevScalars* sc)
+                           const int* __restrict__ perm, const float4* __restrict__ of,
+                           const int* __restrict__ ccell, float rcf, float rc2f, DevScalars* sc)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -399,11 +445,21 @@ __global__ void k_csr_fill(const double* __restrict__ r0, int n, int dim, int nx
     double Vi = (double)mass[i] / rho0;
     double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     double sw = 0.0, sw2 = 0.0;
+    const float4 oi = of[i];
+    const int ci = ccell[i];
+    const int row_end = row_ptr[i + 1];
     for_footprint(cell_of[i], dim, nx, ny, nz, start, [&](int a, int b, int off) {
         for (int j = a; j < b; ++j) {
             if (j == i) continue;
+            // the same decisions as k_csr_count, so the row fills exactly
+            const int pre = near_prefilter(dim, oi, ci, of[j], ccell[j], rcf, rc2f);
+            if (pre == 0) continue;
             double d2 = dist2(dim, r0, n, i, j);
-            if (!(d2 > 0.0 && d2 < rc2)) continue;
+            if (pre < 0 && !(d2 > 0.0 && d2 < rc2)) continue;
+            if (k >= row_end) {  // cannot happen with count's decisions; never write past the row
+                if (atomicCAS(&sc->status, DEV_OK, DEV_NONFINITE) == DEV_OK) sc->err_index = i;
+                continue;
+            }
             double r = sqrt(d2);
             double f = wendland_dw_over_r(dim, h, r);
             double Vj = (double)mass[j] / rho0;
@@ -707,8 +763,13 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_TRY(dalloc(b, &deg, n));
     SRDR_TRY(dalloc(b, &b->row_ptr, (size_t)n + 1));
     double rc2 = b->rc * b->rc;
+    float4* pof = nullptr;
+    SRDR_TRY(dalloc(b, &pof, n));
+    SRDR_TRY(dalloc(b, &b->ccell, n));
+    k_cell_pos_f<<<nblocks(n), kThreads, 0, st>>>(b->r0, n, g, b->cell_of, pof, b->ccell);
+    const float rcf = (float)b->rc, rc2f = (float)rc2;
     k_csr_count<<<nblocks(n), kThreads, 0, st>>>(b->r0, n, dim, g.nx, g.ny, g.nz, b->cell_start,
-                                                 b->cell_of, rc2, deg);
+                                                 b->cell_of, pof, b->ccell, rcf, rc2f, rc2, deg);
     SRDR_TRY(scan_exclusive(deg, b->row_ptr, n, tmp, st));
     int nnz = 0;
     SRDR_CK(cudaMemcpyAsync(&nnz, b->row_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -739,14 +800,13 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     k_csr_fill<T><<<nblocks(n), kThreads, 0, st>>>(b->r0, n, dim, g.nx, g.ny, g.nz, b->cell_start,
                                                    b->cell_of, rc2, b->h, b->desc.rho0, mass,
                                                    b->row_ptr, b->col, b->loc, w, sumw, sumw2, B0,
-                                                   b->perm, b->sc);
+                                                   b->perm, pof, b->ccell, rcf, rc2f, b->sc);
     SRDR_CK(cudaGetLastError());
 
     // per-particle cell offsets and packed cells, then G_i from the same pair
     // gradient the passes evaluate
     T* cpos = nullptr;
     SRDR_TRY(dalloc(b, &cpos, (size_t)n * 4));
-    SRDR_TRY(dalloc(b, &b->ccell, n));
     b->cpos = cpos;
     k_cell_pos<T><<<nblocks(n), kThreads, 0, st>>>(b->r0, n, g, b->cell_of, mass, b->desc.rho0, cpos,
                                                    b->ccell);
@@ -825,13 +885,18 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_CK(cudaStreamSynchronize(st));
     for (void* p : {(void*)r0aos, (void*)vol, (void*)u0, (void*)fl, (void*)bpart, (void*)bbox,
                     (void*)cell_orig, (void*)count, (void*)fill, (void*)ccount, (void*)cfill,
-                    (void*)deg, (void*)slots, (void*)fs, (void*)tmp})
+                    (void*)deg, (void*)slots, (void*)fs, (void*)tmp, (void*)pof})
         SRDR_TRY(dev_free(b, p));
     SRDR_CK(cudaStreamSynchronize(st));
     if (b->sc_host) {
         SRDR_CK(cudaMemcpy(b->sc_host, b->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
         if (b->sc_host->status == DEV_SINGULAR_B0) {
             set_error("singular correction matrix at particle (sorted index) %lld",
+                      (long long)b->sc_host->err_index);
+            return SRDR_ERR_INVALID;
+        }
+        if (b->sc_host->status != DEV_OK) {
+            set_error("neighbour rows inconsistent at particle (sorted index) %lld",
                       (long long)b->sc_host->err_index);
             return SRDR_ERR_INVALID;
         }
