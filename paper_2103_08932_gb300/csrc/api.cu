@@ -281,14 +281,23 @@ __global__ void k_read_uv(const int* __restrict__ perm, int n, const double* __r
                           const float* __restrict__ uhi, const float* __restrict__ ulo,
                           const T* __restrict__ v, double half_dt, int what, double* __restrict__ out)
 {
+    (void)ulo;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
+    float hf[3] = {0, 0, 0}, lf[3] = {0, 0, 0};
+    if (!u) {
+        const float4 r = reinterpret_cast<const float4*>(uhi)[s];
+        hf[0] = r.x;
+        hf[1] = r.y;
+        hf[2] = r.z;
+        lo_decode(hf, r.w, lf);
+    }
     for (int a = 0; a < 3; ++a) {
         double vv = (double)v[(size_t)s * 4 + a];
         double x;
         if (what == 0) {
-            double uh = u ? u[(size_t)s * 4 + a] : (double)uhi[(size_t)s * 4 + a] + (double)ulo[(size_t)s * 4 + a];
+            double uh = u ? u[(size_t)s * 4 + a] : (double)hf[a] + (double)lf[a];
             x = uh - half_dt * vv;  // u^n = u^{n+1/2} - dt/2 v^n
         } else {
             x = vv;
@@ -302,9 +311,11 @@ __global__ void k_write_uv(const int* __restrict__ perm, int n, const double* __
                            const double* __restrict__ vin, double half_dt, double* __restrict__ u,
                            float* __restrict__ uhi, float* __restrict__ ulo, T* __restrict__ v)
 {
+    (void)ulo;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
+    float h[3] = {0, 0, 0}, l[3] = {0, 0, 0};
     for (int a = 0; a < 3; ++a) {
         double vv = vin ? vin[(size_t)i * 3 + a] : (double)v[(size_t)s * 4 + a];
         if (vin) v[(size_t)s * 4 + a] = (T)vv;
@@ -313,12 +324,12 @@ __global__ void k_write_uv(const int* __restrict__ perm, int n, const double* __
             if (u) {
                 u[(size_t)s * 4 + a] = x;
             } else {
-                float h = (float)x;
-                uhi[(size_t)s * 4 + a] = h;
-                ulo[(size_t)s * 4 + a] = (float)(x - (double)h);
+                h[a] = (float)x;
+                l[a] = (float)(x - (double)h[a]);
             }
         }
     }
+    if (uin && !u) reinterpret_cast<float4*>(uhi)[s] = make_float4(h[0], h[1], h[2], lo_encode(h, l));
 }
 
 template <typename T>

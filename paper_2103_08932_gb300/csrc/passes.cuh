@@ -29,8 +29,8 @@ __device__ inline uint16_t ld_stream(const uint16_t* p)
 }
 
 // ------------------------------------------------------------------ layouts
-// u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 hi and lo arrays
-// [n][4] each (u = hi + lo).
+// u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 records [n][4]
+// (hi x, y, z and the packed lo of lo_encode; u = hi + lo).
 // PB (P B0): the D x D entries of a particle, row-major, in pb_chunks
 // 16-byte chunks; chunk c of all particles forms one dense array, chunk c of
 // particle j at 16-byte index c n + j.  A neighbour gather then reads one
@@ -119,14 +119,13 @@ struct UAcc<double> {
 };
 template <>
 struct UAcc<float> {
-    // FP32 mixed: u = hi + lo, two float4 arrays (about 48 significant bits)
-    __device__ static void load(const double*, const float* hi, const float* lo, int j, float (&h)[3],
+    // FP32 mixed: one record (hi x, y, z, packed lo), u = hi + lo
+    __device__ static void load(const double*, const float* hi, const float*, int j, float (&h)[3],
                                 float (&l)[3])
     {
         const float4 a = __ldg(reinterpret_cast<const float4*>(hi) + j);
-        const float4 b = __ldg(reinterpret_cast<const float4*>(lo) + j);
         h[0] = a.x; h[1] = a.y; h[2] = a.z;
-        l[0] = b.x; l[1] = b.y; l[2] = b.z;
+        lo_decode(h, a.w, l);
     }
     // (hi_i - hi_j) + (lo_i - lo_j): the hi difference is exact when the two
     // displacements are within a factor of two (Sterbenz), which is exactly
@@ -399,7 +398,8 @@ __device__ inline void ke_finalize(const double* __restrict__ part, int np, DevS
     }
 }
 
-// u <- u + d, FP64 or FP32 hi/lo (two-sum with renormalisation)
+// u <- u + d, FP64, or FP32 hi + packed lo (two-sum with renormalisation,
+// then lo re-encoded)
 template <typename T>
 __device__ inline void u_add(const StepArgs<T>& a, int i, const T (&d)[3]);
 template <>
@@ -427,13 +427,12 @@ template <>
 __device__ inline void u_add<float>(const StepArgs<float>& a, int i, const float (&d)[3])
 {
     float4* ph = reinterpret_cast<float4*>(a.uhi) + i;
-    float4* pl = reinterpret_cast<float4*>(a.ulo) + i;
-    float4 h = *ph, l = *pl;
-    two_sum_add(h.x, l.x, d[0]);
-    two_sum_add(h.y, l.y, d[1]);
-    two_sum_add(h.z, l.z, d[2]);
-    *ph = h;
-    *pl = l;
+    float4 r = *ph;
+    float h[3] = {r.x, r.y, r.z}, l[3];
+    lo_decode(h, r.w, l);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) two_sum_add(h[c], l[c], d[c]);
+    *ph = make_float4(h[0], h[1], h[2], lo_encode(h, l));
 }
 
 // ------------------------------------------------------------------ pass B
@@ -636,7 +635,7 @@ StepArgs<T> make_step_args(srdr_body* b)
     a.v = static_cast<T*>(b->v);
     a.u = b->u;
     a.uhi = b->uhi;
-    a.ulo = b->ulo;
+    a.ulo = nullptr;
     a.flags = b->flags;
     a.mass = static_cast<const T*>(b->mass);
     a.ke_part = b->ke_part;

@@ -266,15 +266,20 @@ __global__ void k_gather(const int* __restrict__ perm, int n, const double* __re
     const double m = rho0 * (vol ? vol[i] : vol0);
     mass[s] = (T)m;
     minv[s] = (T)(1.0 / m);
-    // u at the half step, AoS padded to 4: FP64 [n][4] or FP32 hi/lo [n][4]
+    // u at the half step, AoS padded to 4: FP64 [n][4] or FP32 records
+    // (hi x, y, z, packed lo)
+    float h[3], l[3];
     for (int a = 0; a < 4; ++a) {
         double x = (u0 && a < 3) ? u0[(size_t)i * 3 + a] : 0.0;
         if (u) u[(size_t)s * 4 + a] = x;
-        if (uhi) {
-            float hi = (float)x;
-            uhi[(size_t)s * 4 + a] = hi;
-            ulo[(size_t)s * 4 + a] = (float)(x - (double)hi);
+        if (a < 3) {
+            h[a] = (float)x;
+            l[a] = (float)(x - (double)h[a]);
         }
+    }
+    if (uhi) {
+        (void)ulo;
+        reinterpret_cast<float4*>(uhi)[s] = make_float4(h[0], h[1], h[2], lo_encode(h, l));
     }
 }
 
@@ -728,7 +733,6 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
         SRDR_TRY(dalloc(b, &b->u, (size_t)n * 4));
     } else {
         SRDR_TRY(dalloc(b, &b->uhi, (size_t)n * 4));
-        SRDR_TRY(dalloc(b, &b->ulo, (size_t)n * 4));
     }
     k_gather<T><<<nblocks(n), kThreads, 0, st>>>(b->perm, n, r0aos, vol, b->vol0, fl, u0, cell_orig,
                                                  b->desc.rho0, b->inv, b->cell_of, b->r0, b->flags,

@@ -5,9 +5,10 @@
 // sorted by (cell id, original id), the canonical order of the splitting
 // cell-linked list):
 //   r0    FP64 [3][n] SoA reference positions
-//   u     FP64 [n][4] (FP64 mode) or FP32 hi and lo arrays [n][4] (FP32 mode,
-//         u = hi + lo), held at the half step u^{n+1/2}; AoS so that one
-//         neighbour gather is one or two 16-byte loads
+//   u     FP64 [n][4] (FP64 mode) or FP32 records [n][4] (FP32 mode: hi and
+//         a packed 10-bit lo, u = hi + lo), held at the half step
+//         u^{n+1/2}; AoS so that one neighbour gather is one (FP32) or two
+//         (FP64) 16-byte loads
 //   v     T [n][4] velocity records (vx, vy, vz, 1/m): one 16-byte (FP32) or
 //         two 16-byte (FP64) accesses per particle
 //   B0    T [D*D][n] row-major tensor components, SoA (read by the owner only)
@@ -63,6 +64,43 @@ struct DevScalars {
     long long err_index;   // first offending particle / cell for status
 };
 
+// FP32-mixed displacement record (float4): x, y, z hold hi = fl(u); w holds
+// lo = u - hi of each component as a signed 10-bit multiple of ulp(hi)/1024
+// (|lo| <= ulp(hi)/2 after renormalisation).  u = hi + lo then carries about
+// 35 significant bits, and a neighbour gather is one 16-byte load.  ulp/1024
+// and its inverse are powers of two, so scaling is exact; |hi| < 2^-93
+// keeps lo = 0.
+__device__ inline float lo_unit(float h)
+{
+    const unsigned e = (__float_as_uint(h) >> 23) & 0xffu;
+    return e > 33u ? __uint_as_float((e - 33u) << 23) : 0.0f;
+}
+__device__ inline float lo_inv_unit(float h)
+{
+    const unsigned e = (__float_as_uint(h) >> 23) & 0xffu;
+    return (e > 33u && e < 255u) ? __uint_as_float((287u - e) << 23) : 0.0f;
+}
+__device__ inline float lo_encode(const float (&h)[3], const float (&l)[3])
+{
+    unsigned w = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        int q = __float2int_rn(l[c] * lo_inv_unit(h[c]));
+        q = q < -511 ? -511 : (q > 511 ? 511 : q);
+        w |= ((unsigned)q & 1023u) << (10 * c);
+    }
+    return __uint_as_float(w);
+}
+__device__ inline void lo_decode(const float (&h)[3], float packed, float (&l)[3])
+{
+    const unsigned w = __float_as_uint(packed);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int q = (int)(w << (22 - 10 * c)) >> 22;  // sign-extended 10-bit field
+        l[c] = (float)q * lo_unit(h[c]);
+    }
+}
+
 // grid-barrier buffer: kBarSub arrival sub-counters, a top counter and a
 // generation word, each on its own 128-byte line
 constexpr int kBarSub = 32;
@@ -96,8 +134,8 @@ struct StepArgs {
     const int* dflag;            // device-decided damping of this step (graph replay), else null
     T* __restrict__ v;          // [n][4] (vx, vy, vz, 1/m)
     double* __restrict__ u;     // [3][n] FP64 mode
-    float* __restrict__ uhi;    // [n][4] FP32 mode, u = hi + lo
-    float* __restrict__ ulo;    // [n][4] FP32 mode
+    float* __restrict__ uhi;    // [n][4] FP32 mode: (hi x, y, z, packed lo), u = hi + lo
+    float* __restrict__ ulo;    // unused (null)
     const uint8_t* __restrict__ flags;
     const T* __restrict__ mass;
     double* __restrict__ ke_part;
@@ -176,8 +214,8 @@ struct srdr_body {
     void* srd = nullptr;         //   (prepare_sweep; B_j = c w_ij with the body's c)
     void* v = nullptr;          // T [n][4] (vx, vy, vz, 1/m)
     double* u = nullptr;        // FP64 [3][n]
-    float* uhi = nullptr;       // [n][4] FP32 mode
-    float* ulo = nullptr;       // [n][4] FP32 mode
+    float* uhi = nullptr;       // [n][4] FP32 mode: (hi x, y, z, packed lo)
+    float* ulo = nullptr;       // unused (null)
     double* ke_part = nullptr;
     int ke_blocks = 0;
     srdr::DevScalars* sc = nullptr;
@@ -271,7 +309,7 @@ srdr_status prepare_sweep(srdr_body* b);
 // brick size; b->bricks_built = 1 when built, -1 when a halo does not fit
 srdr_status build_bricks(srdr_body* b);
 // shared memory of the tiled passes per block for a halo of h particles
-inline size_t tile_smem_a(size_t tsize, int h) { (void)tsize; return (size_t)32 * h; }
+inline size_t tile_smem_a(size_t tsize, int h) { return (tsize == 4 ? (size_t)16 : (size_t)32) * h; }
 inline size_t tile_smem_b(size_t tsize, int dim, int h) { return 16 * (size_t)pb_chunks(tsize, dim) * h; }
 constexpr size_t kTileSmemMax = 200 * 1024;
 // kernel-class timing (api.cu): begin/end an interval of class k
