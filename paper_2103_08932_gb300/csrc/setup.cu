@@ -785,9 +785,9 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     b->nnz = nnz;
     T *w = nullptr, *sumw = nullptr, *sumw2 = nullptr, *Gs = nullptr, *B0 = nullptr, *PB = nullptr;
     SRDR_TRY(dalloc(b, &b->col, std::max(nnz, 1)));
-    // 4 spare entries: the sweep copies loc as 32-bit words
-    SRDR_TRY(dalloc(b, &b->loc, (size_t)nnz + 4));
-    SRDR_TRY(dalloc(b, &w, std::max(nnz, 1)));
+    // a spare 16-byte chunk each: the sweep stages loc and w in 16-byte chunks
+    SRDR_TRY(dalloc(b, &b->loc, (size_t)nnz + 8));
+    SRDR_TRY(dalloc(b, &w, (size_t)nnz + 16 / sizeof(T)));
     SRDR_TRY(dalloc(b, &sumw, n));
     SRDR_TRY(dalloc(b, &sumw2, n));
     SRDR_TRY(dalloc(b, &Gs, (size_t)n * 3));

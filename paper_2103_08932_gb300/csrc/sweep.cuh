@@ -9,13 +9,14 @@
 // a bounded grid barrier in one cooperative launch.
 //
 // Mapping: a warp holds G cells, one group of L = 32/G lanes per cell.  A
-// group stages in shared memory its cell's CSR rows, weights and
-// per-particle constants (read-only, by cp.async) and its footprint's
-// velocity records (v, 1/m) (through L2: other SMs wrote them in earlier
-// colour phases), then updates the cell's particles one after another, its
-// lanes spread over each particle's neighbours.  The read-only part of the
-// group's next cell is requested before the grid barrier that precedes it,
-// so only the velocities are fetched after the barrier; inside the chain the
+// group stages in shared memory its cell's CSR rows, weights and per-particle
+// constants (read-only, by cp.async), a table of its footprint's particle
+// indices, and its footprint's velocity records (v, 1/m) (cp.async from L2: other SMs
+// wrote them in earlier colour phases), then updates the cell's particles
+// one after another, its lanes spread over each particle's neighbours, each
+// particle's loop only as long as its row.  The read-only part of the group's
+// next cell is requested before the grid barrier that precedes it, so only
+// the velocities are fetched after the barrier; inside the chain the
 // next particle's neighbour indices and weights are read while the current
 // particle's sums are reduced.  More cells per warp give each warp
 // independent work to overlap the serial in-cell chain; fewer give fewer
@@ -40,6 +41,11 @@ __device__ inline void cp_async_t(T* dst, const T* src)
     else
         cp_async4(dst, src);
 }
+__device__ inline void cp_async16s(void* dst, const void* src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- footprint runs
@@ -52,14 +58,6 @@ struct FootRuns {
     int total;
     int a[9];
     int off[10];
-    __device__ int particle(int q) const
-    {
-        int j = 0;
-#pragma unroll
-        for (int r = 0; r < 9; ++r)
-            if (r < nruns && q >= off[r]) j = a[r] + (q - off[r]);
-        return j;
-    }
 };
 
 template <int L>
@@ -155,12 +153,16 @@ __device__ inline bool bar_wait(unsigned* bar, unsigned g, DevScalars* sc)
 }
 
 // ---------------------------------------------------------------- shared memory
-// Per cell (group):
+// Per cell (group), each section on a 16-byte boundary:
 //   sv [F + 1] footprint velocity records (vx, vy, vz, 1/m) and a zero
-//   record at F that padded neighbour slots point at, sw [P] weights,
+//   record at F that padded neighbour slots point at,
+//   sw [P + 2E] CSR weights, copied in 16-byte chunks from the chunk holding
+//   the cell's first row entry (E = 16 / sizeof(T) entries per chunk),
 //   sm / sbm / srd [C] per particle of the cell: mass, sum_B - m_i and
 //   1 / ((sum_B - m_i)^2 + sum_B^2) (precomputed per body),
-//   srow [C+1] absolute row starts, sl [P+4] footprint-local indices (uint16)
+//   srow [C+1] absolute row starts,
+//   sl [P + 16] footprint-local indices (uint16), 16-byte chunks like sw,
+//   sfoot [F] the sorted particle index of each footprint-local index.
 template <typename T, int D>
 struct CellSmem {
     vec4_t<T>* sv;
@@ -170,31 +172,47 @@ struct CellSmem {
     T* srd;
     int* srow;
     uint16_t* sl;
+    int* sfoot;
 };
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// byte offsets of the sections after sv: sw, sm (then sbm, srd), srow, sl,
+// sfoot, end
+template <typename T, int D>
+__host__ __device__ inline void cell_smem_offsets(int F, int P, int C, size_t (&o)[6])
+{
+    constexpr int E = 16 / (int)sizeof(T);
+    o[0] = align16(sizeof(T) * 4 * ((size_t)F + 1));
+    o[1] = o[0] + align16(sizeof(T) * ((size_t)P + 2 * E));
+    o[2] = o[1] + align16(sizeof(T) * 3 * (size_t)C);
+    o[3] = o[2] + align16(sizeof(int) * ((size_t)C + 1));
+    o[4] = o[3] + align16(sizeof(uint16_t) * ((size_t)P + 16));
+    o[5] = o[4] + align16(sizeof(int) * (size_t)F);
+}
 
 template <typename T, int D>
 __host__ __device__ inline size_t cell_smem_bytes(int F, int P, int C)
 {
-    size_t b = sizeof(T) * (4 * ((size_t)F + 1) + (size_t)P + 3 * (size_t)C);
-    b = (b + 3) & ~size_t(3);
-    b += sizeof(int) * ((size_t)C + 1);
-    b += sizeof(uint16_t) * ((size_t)P + 4);
-    return (b + 15) & ~size_t(15);
+    size_t o[6];
+    cell_smem_offsets<T, D>(F, P, C, o);
+    return o[5];
 }
 
 template <typename T, int D>
 __device__ inline CellSmem<T, D> cell_smem(unsigned char* raw, int F, int P, int C)
 {
+    size_t o[6];
+    cell_smem_offsets<T, D>(F, P, C, o);
     CellSmem<T, D> s;
     s.sv = reinterpret_cast<vec4_t<T>*>(raw);
-    s.sw = reinterpret_cast<T*>(raw) + 4 * ((size_t)F + 1);
-    s.sm = s.sw + P;
+    s.sw = reinterpret_cast<T*>(raw + o[0]);
+    s.sm = reinterpret_cast<T*>(raw + o[1]);
     s.sbm = s.sm + C;
     s.srd = s.sbm + C;
-    size_t off = sizeof(T) * (4 * ((size_t)F + 1) + (size_t)P + 3 * (size_t)C);
-    off = (off + 3) & ~size_t(3);
-    s.srow = reinterpret_cast<int*>(raw + off);
-    s.sl = reinterpret_cast<uint16_t*>(s.srow + C + 1);
+    s.srow = reinterpret_cast<int*>(raw + o[2]);
+    s.sl = reinterpret_cast<uint16_t*>(raw + o[3]);
+    s.sfoot = reinterpret_cast<int*>(raw + o[4]);
     return s;
 }
 
@@ -233,13 +251,23 @@ __device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellS
     st.p0 = __ldg(a.row_ptr + st.cs);
     st.p1 = __ldg(a.row_ptr + ce);
     const int p0 = st.p0, p1 = st.p1, np = st.np;
-    for (int k = p0 + gl; k < p1; k += L) cp_async_t(s.sw + (k - p0), a.w + k);
     {
-        // footprint-local indices as 32-bit words from an even start
-        const int w0 = p0 >> 1, w1 = (p1 + 1) >> 1;
-        const uint32_t* lw = reinterpret_cast<const uint32_t*>(a.loc);
-        uint32_t* sw32 = reinterpret_cast<uint32_t*>(s.sl);
-        for (int k = w0 + gl; k < w1; k += L) cp_async4(sw32 + (k - w0), lw + k);
+        // weights and footprint-local indices in 16-byte chunks from the
+        // chunk holding entry p0 (the arrays are allocated with a spare
+        // chunk, so the last chunk stays inside them)
+        constexpr int E = 16 / (int)sizeof(T);
+        const int wb = p0 & ~(E - 1);
+        for (int k = wb + gl * E; k < p1; k += L * E) cp_async16s(s.sw + (k - wb), a.w + k);
+        const int lb = p0 & ~7;
+        for (int k = lb + gl * 8; k < p1; k += L * 8) cp_async16s(s.sl + (k - lb), a.loc + k);
+    }
+    // footprint-local index -> sorted particle index
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        if (r < st.fr.nruns) {
+            const int o = st.fr.off[r], len = st.fr.off[r + 1] - o, a0 = st.fr.a[r];
+            for (int q = gl; q < len; q += L) s.sfoot[o + q] = a0 + q;
+        }
     }
     for (int p = gl; p <= np; p += L) cp_async4(s.srow + p, a.row_ptr + st.cs + p);
     for (int p = gl; p < np; p += L) {
@@ -263,29 +291,25 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
     const int np = st.np, p0 = st.p0, my_off = st.my_off;
     const int Ftot = st.fr.total;
     V4* sv = s.sv;
-    const T* sw = s.sw;
+    const T* sw = s.sw + (p0 & (16 / (int)sizeof(T) - 1));  // entry k at sw[k - p0]
+    const int* sfoot = s.sfoot;
     const T cc = a.c;
+    __syncwarp(gmask);  // the footprint table written by other lanes of the group
 
-    // velocity records through L2, in register batches: every load of a
-    // batch is issued before its shared-memory stores
-    constexpr int U = 16;
-    for (int base = 0; base < Ftot; base += L * U) {
-        V4 tv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = base + u * L + gl;
-            if (q < Ftot) tv[u] = ldcg_v4<T>(a.v, st.fr.particle(q));
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = base + u * L + gl;
-            if (q < Ftot) sv[q] = tv[u];
+    // velocity records from L2 straight into shared memory
+    for (int q = gl; q < Ftot; q += L) {
+        const T* src = a.v + (size_t)sfoot[q] * 4;
+        if constexpr (sizeof(T) == 4) {
+            cp_async16s(sv + q, src);
+        } else {
+            cp_async16s(reinterpret_cast<double2*>(sv + q), src);
+            cp_async16s(reinterpret_cast<double2*>(sv + q) + 1, src + 2);
         }
     }
     if (gl == 0) sv[a.max_foot] = V4{T(0), T(0), T(0), T(0)};
     cp_async_wait_all();
     __syncwarp(gmask);
-    const uint16_t* sl = s.sl + (p0 & 1);  // entry k at sl[k - p0]
+    const uint16_t* sl = s.sl + (p0 & 7);  // entry k at sl[k - p0]
     const int pad = a.max_foot;  // the zero record: padded slots read and write it with B = 0
 
     for (int dir = mode == 1 ? 1 : 0; dir <= (mode == 0 ? 0 : 1); ++dir) {
@@ -323,6 +347,9 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
             const V4 vi4 = sv[li];
             const T vi[3] = {vi4.x, vi4.y, vi4.z};
             const bool in_regs = k1 - k0 <= L * NK;
+            // slot batches holding row entries (the same for every lane of
+            // the group); later batches are all padding and are skipped
+            const int nk = (k1 - k0 + L - 1) / L;
             T acc[V][D];
 #pragma unroll
             for (int w = 0; w < V; ++w)
@@ -331,7 +358,8 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
             V4 vj[NK];
             if (in_regs) {
 #pragma unroll
-                for (int m = 0; m < NK; ++m) vj[m] = sv[jj[m]];
+                for (int m = 0; m < NK; ++m)
+                    if (m < nk) vj[m] = sv[jj[m]];
             }
             // the next particle's slots (read-only data)
             int jn[NK];
@@ -341,9 +369,11 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
             if (in_regs) {
 #pragma unroll
                 for (int m = 0; m < NK; ++m) {
-                    const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
+                    if (m < nk) {
+                        const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
 #pragma unroll
-                    for (int d = 0; d < D; ++d) acc[m % V][d] -= BB[m] * (vi[d] - vjd[d]);
+                        for (int d = 0; d < D; ++d) acc[m % V][d] -= BB[m] * (vi[d] - vjd[d]);
+                    }
                 }
             } else {
                 for (int kb = k0 + gl; kb < k1; kb += 32) {
@@ -382,12 +412,14 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
                 // padded slots write the zero record back unchanged (B = 0)
 #pragma unroll
                 for (int m = 0; m < NK; ++m) {
-                    const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
-                    T o[3] = {vjd[0], vjd[1], vjd[2]};
+                    if (m < nk) {
+                        const T vjd[3] = {vj[m].x, vj[m].y, vj[m].z};
+                        T o[3] = {vjd[0], vjd[1], vjd[2]};
 #pragma unroll
-                    for (int d = 0; d < D; ++d)
-                        o[d] = vjd[d] - BB[m] * (vin[d] - vjd[d] + BB[m] * kk[d]) * vj[m].w;
-                    sv[jj[m]] = V4{o[0], o[1], o[2], vj[m].w};
+                        for (int d = 0; d < D; ++d)
+                            o[d] = vjd[d] - BB[m] * (vin[d] - vjd[d] + BB[m] * kk[d]) * vj[m].w;
+                        sv[jj[m]] = V4{o[0], o[1], o[2], vj[m].w};
+                    }
                 }
             } else {
                 for (int k = k0 + gl; k < k1; k += L) {
@@ -449,7 +481,7 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
     }
     }  // dir
     // write the footprint back (through L2: other SMs read it after the barrier)
-    for (int q = gl; q < Ftot; q += L) stcg_v4<T>(a.v, st.fr.particle(q), sv[q]);
+    for (int q = gl; q < Ftot; q += L) stcg_v4<T>(a.v, sfoot[q], sv[q]);
     __syncwarp(gmask);
 }
 
