@@ -324,6 +324,8 @@ def run_gpu(args):
                        "damped_steps": damped, "parallelism": f"replicas{world}",
                        "pass_mapping": {1: "sliced-ELL", 2: "bricks"}.get(st1.get("pass_mapping"), "?"),
                        "sweep_cells_per_warp": st1.get("sweep_cells_per_warp"),
+                       "sweep_sync": {srdr.SRDR_SWEEP_CELLS: "cell-wise waits",
+                                      srdr.SRDR_SWEEP_BARRIER: "grid barriers"}.get(st1.get("sweep_sync")),
                        "l2": "working set ~0.9 GB > 129 MB L2 (no flush)"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

@@ -139,7 +139,9 @@ srdr_status srdr_body_step(srdr_body* body, int64_t nsteps);
 /* Step until KE < ke_ratio * KE_max (KE over free particles, FP64, tested
  * after every step) or max_steps more steps; the state stops at the step that
  * met the criterion.  SRDR_ERR_NOT_CONVERGED at the cap, SRDR_ERR_NONFINITE if
- * KE became non-finite.  steps_taken / final_ke_ratio may be NULL. */
+ * KE became non-finite, SRDR_ERR_TIMEOUT if a bounded wait of the damping
+ * sweep ran out (see srdr_body_sweep_sync).  steps_taken / final_ke_ratio may
+ * be NULL. */
 srdr_status srdr_body_relax(srdr_body* body, double ke_ratio, int64_t max_steps,
                             int64_t* steps_taken, double* final_ke_ratio);
 
@@ -167,6 +169,9 @@ typedef struct {
     int sweep_cells_per_warp; /* damping-sweep mapping picked by the autotuner (1, 2, 4) */
     int pass_mapping;      /* mapping the stress and force passes use: SRDR_PASS_SELL or
                               SRDR_PASS_BRICKS (SRDR_PASS_AUTO before the first step) */
+    int sweep_sync;        /* synchronisation of the sweep's colour phases in use:
+                              SRDR_SWEEP_CELLS or SRDR_SWEEP_BARRIER (SRDR_SWEEP_AUTO
+                              before the first damped step) */
 } srdr_stats;
 srdr_status srdr_body_stats(const srdr_body* body, srdr_stats* out);
 
@@ -208,6 +213,32 @@ srdr_status srdr_body_profile(srdr_body* body, int enable);
  * default).  The choice changes speed only: the sweep's sums follow one fixed
  * order, so results are bitwise the same. */
 srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp, int sweep_warps_per_block);
+
+/* Synchronisation of the damping sweep's colour phases (Sec. 3.4: cells of
+ * one colour run concurrently, colours one after another).
+ * SRDR_SWEEP_BARRIER: a grid barrier between consecutive colour phases.
+ * SRDR_SWEEP_CELLS: no barrier; before each of its phases a cell waits only
+ * for the cells whose footprints overlap its own (within 2 cells on every
+ * axis) to have finished their earlier phases, so the order of every pair of
+ * cells that interact is the canonical one.  SRDR_SWEEP_AUTO (the default):
+ * the autotuner times both with the cells-per-warp choices of
+ * srdr_body_tune (which must then be left to the autotuner for AUTO to take
+ * effect; a fixed mapping uses SRDR_SWEEP_CELLS unless BARRIER is asked).
+ * Results are bitwise the same under every choice.  Every wait is bounded
+ * (one second); a sweep whose wait runs out sets the body's status, and
+ * srdr_body_relax returns SRDR_ERR_TIMEOUT after resetting the
+ * synchronisation words (the velocity state is then that of a partial sweep:
+ * restore it with srdr_body_write_state).  Returns SRDR_ERR_INVALID for
+ * another mode. */
+enum { SRDR_SWEEP_AUTO = 0, SRDR_SWEEP_BARRIER = 1, SRDR_SWEEP_CELLS = 2 };
+srdr_status srdr_body_sweep_sync(srdr_body* body, int mode);
+
+/* Test hook of the failure path above: makes every wait of the body's next
+ * damping sweep run out (it sets the synchronisation words to counts that no
+ * cell reaches), so that the sweep ends with the body's status set after
+ * about a second.  Nothing else changes; the next srdr_body_relax reports
+ * SRDR_ERR_TIMEOUT and resets the words. */
+srdr_status srdr_body_debug_stall_sweep(srdr_body* body);
 
 /* Kernel mapping of the stress and force passes (Sec. 2.2-2.3 and the
  * momentum equation).  SRDR_PASS_SELL: each thread streams its particle's

@@ -38,6 +38,16 @@ srdr_status dev_alloc(srdr_body* b, void** p, size_t bytes)
     return SRDR_OK;
 }
 
+// zero the damping sweep's grid-barrier and cell-wise words (left mid-sweep
+// by a wait that ran out)
+srdr_status reset_sync_words(srdr_body* b)
+{
+    if (b->bar) SRDR_CK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * kBarWords, b->stream));
+    if (b->flow) SRDR_CK(cudaMemsetAsync(b->flow, 0, sizeof(unsigned) * flow_words(b->ncells), b->stream));
+    SRDR_CK(cudaStreamSynchronize(b->stream));
+    return SRDR_OK;
+}
+
 srdr_status dev_free(srdr_body* b, void* p)
 {
     if (!p) return SRDR_OK;
@@ -433,6 +443,12 @@ srdr_status srdr_body_relax(srdr_body* b, double ke_ratio, int64_t max_steps, in
         left -= k;
         SRDR_TRY(sync_scalars(b));
         b->step = b->sc_host->step;
+        if (b->sc_host->status == DEV_TIMEOUT) {
+            SRDR_TRY(reset_sync_words(b));
+            set_error("a bounded wait of the damping sweep ran out (before step %lld)", (long long)b->step);
+            result = SRDR_ERR_TIMEOUT;
+            break;
+        }
         if (b->sc_host->done) {
             if (b->sc_host->status == DEV_NONFINITE) {
                 set_error("kinetic energy became non-finite at step %lld", (long long)b->step);
@@ -526,6 +542,7 @@ srdr_status srdr_body_write_state(srdr_body* b, const double* u, const double* v
     SRDR_TRY(dev_free(b, du));
     SRDR_TRY(dev_free(b, dv));
     SRDR_TRY(sync_scalars(b));
+    if (b->sc_host->status == DEV_TIMEOUT) SRDR_TRY(reset_sync_words(b));
     DevScalars s = *b->sc_host;
     s.step = step_index;
     s.ke_max = ke_max;
@@ -567,6 +584,7 @@ srdr_status srdr_body_stats(const srdr_body* b, srdr_stats* out)
     out->launches = b->launches;
     out->sweep_cells_per_warp = b->sweep_cells_per_warp;
     out->pass_mapping = b->pass_tiled < 0 ? SRDR_PASS_AUTO : (b->pass_tiled ? SRDR_PASS_BRICKS : SRDR_PASS_SELL);
+    out->sweep_sync = !b->sweep_tuned ? SRDR_SWEEP_AUTO : (b->sweep_cellwise ? SRDR_SWEEP_CELLS : SRDR_SWEEP_BARRIER);
     return SRDR_OK;
 }
 
@@ -590,7 +608,42 @@ srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp, int warps_per_block
         b->sweep_tuned = 1;
         b->sweep_cells_per_warp = cells_per_warp;
         b->sweep_warps_per_block = warps_per_block;
+        b->sweep_cellwise = b->sweep_sync != SRDR_SWEEP_BARRIER;
     }
+    return SRDR_OK;
+}
+
+srdr_status srdr_body_sweep_sync(srdr_body* b, int mode)
+{
+    if (!b || mode < SRDR_SWEEP_AUTO || mode > SRDR_SWEEP_CELLS) {
+        set_error("sweep synchronisation must be SRDR_SWEEP_AUTO, SRDR_SWEEP_BARRIER or SRDR_SWEEP_CELLS");
+        return SRDR_ERR_INVALID;
+    }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);  // captured with the old kernel
+        b->graph = nullptr;
+    }
+    b->sweep_sync = mode;
+    if (mode == SRDR_SWEEP_AUTO)
+        b->sweep_tuned = 0;
+    else
+        b->sweep_cellwise = mode == SRDR_SWEEP_CELLS;
+    return SRDR_OK;
+}
+
+srdr_status srdr_body_debug_stall_sweep(srdr_body* b)
+{
+    if (!b || !b->bar || !b->flow) {
+        set_error("bad body");
+        return SRDR_ERR_INVALID;
+    }
+    // a grid-barrier sub-counter that its last arrival never matches, and an
+    // epoch far above every cell's count: every wait of the next sweep runs out
+    const unsigned big = 0x40000000u;
+    SRDR_CK(cudaMemcpyAsync(b->bar, &big, sizeof(unsigned), cudaMemcpyHostToDevice, b->stream));
+    SRDR_CK(cudaMemcpyAsync(b->flow + flow_epoch_word(b->ncells), &big, sizeof(unsigned),
+                            cudaMemcpyHostToDevice, b->stream));
+    SRDR_CK(cudaStreamSynchronize(b->stream));
     return SRDR_OK;
 }
 

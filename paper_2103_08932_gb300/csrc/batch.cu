@@ -627,6 +627,11 @@ srdr_status batch_steps(srdr_batch* bt, int64_t nsteps, double tol, int64_t chec
         SRDR_CK(cudaStreamSynchronize(bt->stream));
         gathered = true;
         if (bt->gathered_h[nb].status == DEV_TIMEOUT) {
+            // the barrier words are left mid-sweep: reset them and the status
+            DevScalars z{};
+            SRDR_CK(cudaMemsetAsync(bt->bar, 0, kBarWords * sizeof(unsigned), bt->stream));
+            SRDR_CK(cudaMemcpyAsync(bt->status, &z, sizeof(z), cudaMemcpyHostToDevice, bt->stream));
+            SRDR_CK(cudaStreamSynchronize(bt->stream));
             set_error("batched damping sweep: a grid barrier timed out");
             return SRDR_ERR_TIMEOUT;
         }

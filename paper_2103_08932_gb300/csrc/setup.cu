@@ -865,6 +865,8 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     b->max_cell = hfs[2];
     SRDR_TRY(dalloc(b, &b->bar, kBarWords));
     SRDR_CK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * kBarWords, st));
+    SRDR_TRY(dalloc(b, &b->flow, flow_words(ncells)));
+    SRDR_CK(cudaMemsetAsync(b->flow, 0, sizeof(unsigned) * flow_words(ncells), st));
     if (b->max_foot >= 65536) {
         set_error("a cell footprint holds %d particles (limit 65535)", b->max_foot);
         return SRDR_ERR_INVALID;

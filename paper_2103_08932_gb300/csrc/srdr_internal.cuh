@@ -246,6 +246,9 @@ struct srdr_body {
     int sweep_warps_per_block = 1;   // warps per block of the sweep kernel (1, 4)
     int sweep_tuned = 0;
     int sweep_smem = 0;
+    int sweep_sync = SRDR_SWEEP_AUTO;  // requested synchronisation of the sweep's colour phases
+    int sweep_cellwise = 1;            // the one in use: cell-wise waits (1) or grid barriers (0)
+    unsigned* flow = nullptr;          // cell-wise synchronisation words (k_sweep_flow)
 
     // host mirrors
     int64_t step = 0;
@@ -287,6 +290,12 @@ inline double kernel_kc(int dim, double h)
     const double a = dim == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
     return -5.0 * a / (h * h);
 }
+
+// cell-wise synchronisation words of the sweep: a counter per cell of the
+// grid, then the epoch at flow_epoch_word and the finished-group count 32
+// words later (each on its own 128-byte line)
+__host__ __device__ inline int flow_epoch_word(int ncells) { return (ncells + 31) & ~31; }
+__host__ __device__ inline int flow_words(int ncells) { return flow_epoch_word(ncells) + 64; }
 
 // elements per particle of the AoS P B0 array (whole 16-byte vectors)
 // 16-byte chunks holding the dim x dim entries of one P B0 (FP32 3D: 3,

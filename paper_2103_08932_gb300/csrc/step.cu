@@ -77,15 +77,17 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     return s;
 }
 
-// The sweep kernel for G cells per warp and W warps per block, its shared
-// memory and its grid (co-resident blocks, at most one group per cell of the
-// widest colour).
+// The sweep kernel for G cells per warp and W warps per block with grid
+// barriers or cell-wise waits, its shared memory, its grid (co-resident
+// blocks, at most one group per cell of the widest colour) and its
+// synchronisation words (its last argument).
 template <typename T, int D>
 struct SweepLaunch {
     const void* fn = nullptr;
     size_t smem = 0;
     int grid = 0;
     int threads = 32;
+    unsigned* sync = nullptr;
 };
 
 template <typename T, int D, int G, int W>
@@ -96,13 +98,14 @@ srdr_status sweep_launch_gw(srdr_body* b, SweepLaunch<T, D>* out)
         set_error("damping sweep needs %zu bytes of shared memory per block (limit 227 KB)", smem);
         return SRDR_ERR_INVALID;
     }
-    const void* fn = (const void*)k_sweep_all<T, D, G, W>;
+    const void* fn = b->sweep_cellwise ? (const void*)k_sweep_flow<T, D, G, W>
+                                       : (const void*)k_sweep_all<T, D, G, W>;
     if (smem > 48 * 1024)
         SRDR_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, nsm = 0;
     SRDR_CK(cudaGetDevice(&dev));
     SRDR_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    SRDR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_all<T, D, G, W>, 32 * W, smem));
+    SRDR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * W, smem));
     if (per_sm < 1) {
         set_error("damping sweep kernel does not fit on an SM (%zu bytes of shared memory)", smem);
         return SRDR_ERR_INVALID;
@@ -113,6 +116,7 @@ srdr_status sweep_launch_gw(srdr_body* b, SweepLaunch<T, D>* out)
     out->fn = fn;
     out->smem = smem;
     out->threads = 32 * W;
+    out->sync = b->sweep_cellwise ? b->flow : b->bar;
     out->grid = std::max(1, std::min((widest + G * W - 1) / (G * W), per_sm * nsm));
     return SRDR_OK;
 }
@@ -132,9 +136,10 @@ srdr_status sweep_launch(srdr_body* b, SweepLaunch<T, D>* out)
 }
 
 // Autotuner of the sweep's mapping: time G = 1 or 2 cells per warp with
-// W = 1 or 4 warps per block (one warm-up and one timed launch each) on a
-// scratch copy of v (the sweep writes v, the body's state must not change)
-// and keep the fastest.  G = 4 (measured slower on every body tried) stays
+// W = 1 or 4 warps per block, with cell-wise waits and with grid barriers
+// (unless one of them is asked for), one warm-up and one timed launch each,
+// on a scratch copy of v (the sweep writes v, the body's state must not
+// change) and keep the fastest.  G = 4 (measured slower on every body tried) stays
 // available through srdr_body_tune.  The sweep's
 // arithmetic does not depend on the mapping (its reductions follow one
 // 32-lane order), so the choice changes speed, never results.
@@ -150,19 +155,24 @@ srdr_status autotune_sweep(srdr_body* b)
     sw.v = vtmp;
     const int* cptr = b->colour_ptr_d;
     int ncol = b->ncolours;
-    unsigned* bar = b->bar;
-    void* params[] = {&sw, &cptr, &ncol, &bar};
+    unsigned* sync = nullptr;
+    void* params[] = {&sw, &cptr, &ncol, &sync};
     cudaEvent_t e0, e1;
     SRDR_CK(cudaEventCreate(&e0));
     SRDR_CK(cudaEventCreate(&e1));
     float best = 3.0e38f;
-    int best_g = b->sweep_cells_per_warp, best_w = b->sweep_warps_per_block;
+    int best_g = b->sweep_cells_per_warp, best_w = b->sweep_warps_per_block, best_c = b->sweep_cellwise;
+    for (int cw : {1, 0})
     for (int g : {1, 2})
         for (int w : {1, 4}) {
+            if ((cw && b->sweep_sync == SRDR_SWEEP_BARRIER) || (!cw && b->sweep_sync == SRDR_SWEEP_CELLS))
+                continue;
+            b->sweep_cellwise = cw;
             b->sweep_cells_per_warp = g;
             b->sweep_warps_per_block = w;
             SweepLaunch<T, D> sl;
             if (sweep_launch<T, D>(b, &sl) != SRDR_OK) continue;  // e.g. too much shared memory
+            sync = sl.sync;
             SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params, sl.smem,
                                                 b->stream));
             SRDR_CK(cudaEventRecord(e0, b->stream));
@@ -176,10 +186,12 @@ srdr_status autotune_sweep(srdr_body* b)
                 best = ms;
                 best_g = g;
                 best_w = w;
+                best_c = cw;
             }
         }
     b->sweep_cells_per_warp = best_g;
     b->sweep_warps_per_block = best_w;
+    b->sweep_cellwise = best_c;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return dev_free(b, vtmp);
@@ -229,7 +241,7 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
     const int grid = sl.grid;
     const int* cptr = b->colour_ptr_d;
     int ncol = b->ncolours;
-    unsigned* bar = b->bar;
+    unsigned* bar = damping ? sl.sync : b->bar;  // grid barrier or cell-wise words
     if (damping && (!sw.colour_cells || !sw.cell_start || !sw.row_ptr || !sw.loc || !sw.w ||
                     !sw.mass || !sw.sbm || !sw.srd || !sw.v || !cptr || !bar)) {
         set_error("damping sweep tables are not built");

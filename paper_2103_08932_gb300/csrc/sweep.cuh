@@ -101,7 +101,7 @@ __device__ inline FootRuns foot_runs_group(int c, int dim, int nx, int ny, int n
 
 // ---------------------------------------------------------------- grid barrier
 // Bounded, split-phase grid barrier of a cooperative launch (all blocks
-// co-resident).  Words of the barrier buffer (kBarWords unsigned, zeroed at
+// co-resident); the wait gives up after kWaitNs or kWaitPolls.  Words of the barrier buffer (kBarWords unsigned, zeroed at
 // creation), each group on its own 128-byte line:
 //   sub-counter k (k < kBarSub) at 32 k, top counter at 32 kBarSub,
 //   generation at 32 (kBarSub + 1).
@@ -109,7 +109,7 @@ __device__ inline FootRuns foot_runs_group(int c, int dim, int nx, int ny, int n
 // arrival of a sub-counter resets it and arrives at the top counter; the last
 // arrival there resets it and bumps the generation.  Waiters poll the
 // generation (its own line, so polling does not slow the counters) with a
-// sleep and give up after 2^24 polls, setting DEV_TIMEOUT in sc->status, so
+// sleep and give up after one second, setting DEV_TIMEOUT in sc->status, so
 // the host gets an error instead of a hung GPU.  Between arrive and wait a
 // block may do work that does not depend on other blocks.
 __device__ inline unsigned bar_arrive(unsigned* bar, unsigned nblocks)
@@ -134,13 +134,26 @@ __device__ inline unsigned bar_arrive(unsigned* bar, unsigned nblocks)
     return g;
 }
 
+// device clock in nanoseconds
+__device__ inline unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bound of every wait of the sweep: far above one colour phase of any body
+// that fits on the device, short enough for a test to run one out
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr long long kWaitPolls = 1LL << 24;
+
 __device__ inline bool bar_wait(unsigned* bar, unsigned g, DevScalars* sc)
 {
     volatile unsigned* gen = bar + 32 * (kBarSub + 1);
     long long polls = 0;
     bool ok = true;
+    const unsigned long long t0 = global_ns();
     while (*gen == g) {
-        if (++polls > (1LL << 24)) {
+        if ((++polls & 63) == 0 && (global_ns() - t0 > kWaitNs || polls > kWaitPolls)) {
             atomicCAS(&sc->status, DEV_OK, DEV_TIMEOUT);
             ok = false;
             break;
@@ -534,6 +547,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
     constexpr int L = 32 / G;
     if (*(volatile int*)&a.sc->done) return;
     if (a.dflag && *a.dflag == 0) return;  // every block reads the same word: no barrier is left waiting
+    if (*(volatile int*)&a.sc->status == DEV_TIMEOUT) return;  // barrier left mid-sweep: host resets it
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / L, gl = lane % L;
@@ -583,4 +597,133 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
         __syncwarp();
     }
     cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------- cell-wise synchronisation
+// The same S_d without grid barriers.  The canonical order only constrains
+// cells whose footprints overlap, i.e. cells within 2 cells of each other on
+// every axis (5^d - 1 of them; same-colour cells are 3 apart, so none of them
+// shares a colour with the cell).  Each cell counts the phases it has
+// finished; before its phase ph a cell waits until every non-empty cell of
+// its 5^d neighbourhood has finished all of its own phases that precede ph,
+// and its later phases wait in turn for this one.  Every pair of overlapping
+// cells is therefore ordered as in the canonical order, so the result is
+// bitwise that of k_sweep_all; regions of the body that are ready run ahead
+// instead of waiting for the slowest cell of the grid at every phase.
+// Groups take their cells in phase order and all of them are co-resident
+// (cooperative launch), so the lowest unfinished phase always progresses.
+//
+// flow buffer (unsigned, zeroed at creation): done[c] for every cell of the
+// grid (phases finished, counted over all sweeps), then at word
+// fo = ncells rounded up to 32 the epoch (sweeps finished), and at fo + 32
+// the number of groups that have finished this sweep; the last of them
+// advances the epoch.  After e sweeps done[c] = e for cells of the last
+// colour (one fused phase) and 2 e for the others.
+
+// phases of a cell of colour cy that come before phase ph
+__device__ inline unsigned phases_before(int cy, int ph, int ncolours, int clast)
+{
+    unsigned k = cy < ph ? 1u : 0u;
+    if (cy != clast && 2 * ncolours - 1 - cy < ph) ++k;
+    return k;
+}
+
+// Wait until the neighbourhood of cell c is ready for its phase ph.  Each
+// lane polls its share of the neighbour cells; a poll gives up after one
+// second (DEV_TIMEOUT) or when another group has already given up.
+template <typename T, int L>
+__device__ inline bool flow_wait(const SweepArgs<T>& a, const unsigned* done, unsigned epoch, int c, int ph,
+                                 int ncolours, int clast, int gl, unsigned gmask)
+{
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    const int nb = a.dim == 3 ? 125 : 25;
+    bool ok = true;
+    for (int o = gl; o < nb && ok; o += L) {
+        const int dx = o % 5 - 2, dy = (o / 5) % 5 - 2, dz = a.dim == 3 ? o / 25 - 2 : 0;
+        const int x = cx + dx, y = cy + dy, z = cz + dz;
+        if ((dx | dy | dz) == 0 || x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) continue;
+        const int d = x + nx * (y + ny * z);
+        if (__ldg(a.cell_start + d + 1) == __ldg(a.cell_start + d)) continue;  // empty: never runs
+        const int col = x % 3 + 3 * (y % 3) + 9 * (z % 3);
+        const unsigned need = epoch * (col == clast ? 1u : 2u) + phases_before(col, ph, ncolours, clast);
+        long long polls = 0;
+        unsigned long long t0 = 0;
+        while (*(volatile const unsigned*)(done + d) < need) {
+            if (polls == 0) t0 = global_ns();
+            if ((++polls & 63) == 0) {
+                if (*(volatile int*)&a.sc->status != DEV_OK) {
+                    ok = false;
+                    break;
+                }
+                if (global_ns() - t0 > kWaitNs || polls > kWaitPolls) {
+                    atomicCAS(&a.sc->status, DEV_OK, DEV_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+            }
+            __nanosleep(64);
+        }
+    }
+    __threadfence();  // the neighbours' velocity writes before this group's reads
+    return __all_sync(gmask, ok);
+}
+
+template <typename T, int D, int G, int W>
+__global__ void __launch_bounds__(32 * W) k_sweep_flow(SweepArgs<T> a, const int* __restrict__ colour_ptr,
+                                                       int ncolours, unsigned* flow)
+{
+    constexpr int L = 32 / G;
+    if (*(volatile int*)&a.sc->done) return;
+    if (a.dflag && *a.dflag == 0) return;
+    if (*(volatile int*)&a.sc->status == DEV_TIMEOUT) return;  // counts left inconsistent: host resets them
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / L, gl = lane % L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
+    const size_t cell_bytes = cell_smem_bytes<T, D>(a.max_foot, a.max_pairs, a.max_cell);
+    const CellSmem<T, D> s = cell_smem<T, D>(smem_raw + (size_t)(wb * G + g) * cell_bytes, a.max_foot,
+                                             a.max_pairs, a.max_cell);
+    const int q0 = (blockIdx.x * W + wb) * G + g, qs = gridDim.x * W * G;
+    const int fo = flow_epoch_word(a.nx * a.ny * a.nz);
+    unsigned* done = flow;
+    const unsigned epoch = *(volatile const unsigned*)(flow + fo);
+    const int clast = last_colour(colour_ptr, ncolours);
+    int staged = first_item(colour_ptr, ncolours, clast, 0, q0);
+    CellStage st{};
+    if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
+    bool ok = true;
+    for (int ph = 0; ph < 2 * ncolours && ok; ++ph) {
+        const int backward = ph >= ncolours;
+        const int col = backward ? 2 * ncolours - 1 - ph : ph;
+        const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
+        if (c1 == c0 || (backward && col == clast)) continue;
+        const int mode = col == clast ? 2 : backward;
+        for (int cid = c0 + q0; cid < c1; cid += qs) {
+            // staged == cid here: items are visited in the order next_item gives
+            const int cell = __ldg(a.colour_cells + cid);
+            if (!flow_wait<T, L>(a, done, epoch, cell, ph, ncolours, clast, gl, gmask)) {
+                ok = false;
+                break;
+            }
+            run_cell<T, D, L>(a, st, mode, s, gl, gmask);
+            if (gl == 0) {
+                __threadfence();  // the group's write-back (ordered by run_cell's __syncwarp) first
+                atomicAdd(done + cell, 1u);
+            }
+            staged = next_item(colour_ptr, ncolours, clast, ph, cid, q0, qs);
+            if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);
+        }
+    }
+    cp_async_wait_all();  // no copy may land after the group has left
+    if (!ok) return;
+    if (gl == 0) {
+        const unsigned total = gridDim.x * W * G;
+        __threadfence();
+        if (atomicAdd(flow + fo + 32, 1u) == total - 1) {
+            atomicExch(flow + fo + 32, 0u);
+            __threadfence();
+            atomicAdd(flow + fo, 1u);
+        }
+    }
 }

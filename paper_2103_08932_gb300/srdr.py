@@ -20,6 +20,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsrdr.so")
 SRDR_PASS_AUTO = 0
 SRDR_PASS_SELL = 1
 SRDR_PASS_BRICKS = 2
+SRDR_SWEEP_AUTO = 0
+SRDR_SWEEP_BARRIER = 1
+SRDR_SWEEP_CELLS = 2
 SRDR_OK = 0
 SRDR_ERR_INVALID = -1
 SRDR_ERR_NO_MEMORY = -2
@@ -45,7 +48,7 @@ EXPORTS = [
     "srdr_body_read_field", "srdr_body_destroy", "srdr_last_error", "srdr_philox4x64_10",
     "srdr_random_phi", "srdr_body_profile", "srdr_body_kernel_times",
     "srdr_kinetic_energy_noalloc", "srdr_body_tune", "srdr_desc_particle_count",
-    "srdr_body_pass_mapping",
+    "srdr_body_pass_mapping", "srdr_body_sweep_sync", "srdr_body_debug_stall_sweep",
     "srdr_batch_create", "srdr_batch_step", "srdr_batch_run", "srdr_batch_info",
     "srdr_batch_destroy", "srdr_batch_relax", "srdr_server_create", "srdr_server_configure",
     "srdr_server_submit", "srdr_server_poll", "srdr_server_wait", "srdr_server_stats",
@@ -88,7 +91,8 @@ class srdr_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("damped_steps", C.c_int64), ("ke", C.c_double),
                 ("ke_max", C.c_double), ("eta", C.c_double), ("dt", C.c_double),
                 ("converged", C.c_int), ("launches", C.c_int64),
-                ("sweep_cells_per_warp", C.c_int), ("pass_mapping", C.c_int)]
+                ("sweep_cells_per_warp", C.c_int), ("pass_mapping", C.c_int),
+                ("sweep_sync", C.c_int)]
 
 
 class srdr_kernel_times(C.Structure):
@@ -132,6 +136,8 @@ def lib():
         "srdr_body_kernel_times": (st, [p, C.POINTER(srdr_kernel_times)]),
         "srdr_body_tune": (st, [p, C.c_int, C.c_int]),
         "srdr_body_pass_mapping": (st, [p, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "srdr_body_sweep_sync": (st, [p, C.c_int]),
+        "srdr_body_debug_stall_sweep": (st, [p]),
         "srdr_desc_particle_count": (st, [C.POINTER(srdr_body_desc), C.POINTER(i64)]),
         "srdr_batch_create": (st, [p, C.c_int, p, C.POINTER(p)]),
         "srdr_batch_step": (st, [p, i64]),
@@ -272,6 +278,14 @@ class Body:
 
     def tune(self, sweep_cells_per_warp=0, sweep_warps_per_block=0):
         _check(lib().srdr_body_tune(self.h, int(sweep_cells_per_warp), int(sweep_warps_per_block)))
+
+    def sweep_sync(self, mode=0):
+        """SRDR_SWEEP_AUTO (0), SRDR_SWEEP_BARRIER (1) or SRDR_SWEEP_CELLS (2)."""
+        _check(lib().srdr_body_sweep_sync(self.h, int(mode)))
+
+    def debug_stall_sweep(self):
+        """Make every wait of the next damping sweep run out (failure-path test hook)."""
+        _check(lib().srdr_body_debug_stall_sweep(self.h))
 
     def pass_mapping(self, mapping=0, brick=(0, 0, 0)):
         """SRDR_PASS_AUTO (0), SRDR_PASS_SELL (1) or SRDR_PASS_BRICKS (2),

@@ -302,6 +302,75 @@ JIT3D = S.BodySpec(dim=3, extent=(0.013, 0.005, 0.007), dp=1e-3, clamp_axis=0, c
                    alpha=0.5, seed=1)
 
 
+@pytest.mark.parametrize("spec,precision,damping,jit", [
+    (SMALL3D, srdr.SRDR_FP64, srdr.SRDR_DAMP_PARTICLE, False),
+    (SMALL3D, srdr.SRDR_FP32_MIXED, srdr.SRDR_DAMP_PARTICLE, False),
+    (SMALL2D, srdr.SRDR_FP64, srdr.SRDR_DAMP_PARTICLE, False),
+    (SMALL2D, srdr.SRDR_FP32_MIXED, srdr.SRDR_DAMP_PAIRWISE, False),
+    (JIT3D, srdr.SRDR_FP32_MIXED, srdr.SRDR_DAMP_PARTICLE, True),
+    (JIT3D, srdr.SRDR_FP64, srdr.SRDR_DAMP_PAIRWISE, True)])
+def test_sweep_sync_modes_are_bitwise_equal(spec, precision, damping, jit):
+    """Grid barriers between colour phases and cell-wise waits on the
+    overlapping neighbourhood order every pair of interacting cells the same
+    way: velocities agree bit for bit with every cells-per-warp mapping, on
+    directly launched steps and on replayed graphs, with empty cells
+    (jittered particles) and both damping schemes."""
+    parts = S.jittered(spec, 0.3, 5) if jit else None
+    ref = gpu_for(spec, precision=precision, damping=damping, particles=parts)
+    ref.sweep_sync(srdr.SRDR_SWEEP_BARRIER)
+    ref.tune(1, 1)
+    ref.step(14)
+    assert ref.stats()["sweep_sync"] == srdr.SRDR_SWEEP_BARRIER
+    assert 0 < ref.stats()["damped_steps"] < 14
+    ref.step(64)  # replayed graphs for bodies this small
+    for mode in (srdr.SRDR_SWEEP_CELLS, srdr.SRDR_SWEEP_BARRIER, srdr.SRDR_SWEEP_AUTO):
+        for g, w in ((1, 1), (2, 1), (1, 4), (0, 0)):
+            b = gpu_for(spec, precision=precision, damping=damping, particles=parts)
+            b.sweep_sync(mode)
+            b.tune(g, w)
+            b.step(14)
+            st = b.stats()
+            if mode != srdr.SRDR_SWEEP_AUTO:
+                assert st["sweep_sync"] == mode
+            else:
+                assert st["sweep_sync"] in (srdr.SRDR_SWEEP_BARRIER, srdr.SRDR_SWEEP_CELLS)
+            b.step(64)
+            assert np.array_equal(b.velocity(), ref.velocity()), (mode, g, w)
+            assert np.array_equal(b.displacement(), ref.displacement()), (mode, g, w)
+            assert b.stats()["ke"] == ref.stats()["ke"], (mode, g, w)
+
+
+@pytest.mark.parametrize("mode", [srdr.SRDR_SWEEP_CELLS, srdr.SRDR_SWEEP_BARRIER])
+def test_sweep_wait_that_runs_out_is_reported(mode):
+    """Failure path of the sweep's bounded waits: a test hook sets the
+    synchronisation words to counts no cell reaches, every wait of the next
+    sweep gives up after its bound (about a second), relax returns
+    SRDR_ERR_TIMEOUT, and the body stays usable: after restoring a state it
+    steps exactly like an untouched body from that state."""
+    ref = gpu_for(SMALL3D, precision=srdr.SRDR_FP64)
+    ref.sweep_sync(mode)
+    ref.tune(1, 1)
+    ref.step(40)
+    u, v, ke_max = ref.displacement(), ref.velocity(), ref.stats()["ke_max"]
+    ref.write_state(u, v, 40, ke_max)
+    b = gpu_for(SMALL3D, precision=srdr.SRDR_FP64)
+    b.sweep_sync(mode)
+    b.tune(1, 1)
+    b.step(40)
+    b.debug_stall_sweep()
+    status, steps, _ = b.relax(1e-30, 200, check=False)
+    assert status == srdr.SRDR_ERR_TIMEOUT
+    assert "ran out" in srdr.last_error()
+    status, _, _ = b.relax(1e-30, 10, check=False)
+    assert status == srdr.SRDR_ERR_TIMEOUT  # the status holds until a state is written
+    b.write_state(u, v, 40, ke_max)
+    ref.step(30)
+    b.step(30)
+    assert b.stats()["damped_steps"] > 0
+    assert np.array_equal(b.velocity(), ref.velocity())
+    assert np.array_equal(b.displacement(), ref.displacement())
+
+
 @pytest.mark.parametrize("spec,precision,jit", [
     (SMALL3D, srdr.SRDR_FP64, False), (SMALL3D, srdr.SRDR_FP32_MIXED, False),
     (SMALL2D, srdr.SRDR_FP64, False), (SMALL2D, srdr.SRDR_FP32_MIXED, False),
