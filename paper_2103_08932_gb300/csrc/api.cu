@@ -355,10 +355,13 @@ __global__ void k_read_field(const int* __restrict__ perm, int n, int dim, const
             if (p < dim && q < dim) {
                 int k = p * dim + q;
                 if (aos_stride > 0) {
-                    // PB: entry k in 16-byte chunk k / E (E = 16 / sizeof(T)
-                    // entries per chunk), chunk c of particle s at c n + s
-                    const int E = 16 / (int)sizeof(T);
-                    x = (double)src[((size_t)(k / E) * n + s) * E + k % E];
+                    // PB: entry k < F E in 16-byte chunk k / E (E = 16 /
+                    // sizeof(T) entries per chunk, F whole chunks), chunk c
+                    // of particle s at c n + s; leftover entry t = k - F E at
+                    // T index (F E + t) n + s
+                    const int E = 16 / (int)sizeof(T), F = pb_full(sizeof(T), dim);
+                    x = k < F * E ? (double)src[((size_t)(k / E) * n + s) * E + k % E]
+                                  : (double)src[(size_t)k * n + s];
                 } else {
                     x = (double)src[(size_t)k * n + s];
                 }

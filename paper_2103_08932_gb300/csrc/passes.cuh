@@ -31,18 +31,23 @@ __device__ inline uint16_t ld_stream(const uint16_t* p)
 // ------------------------------------------------------------------ layouts
 // u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 records [n][4]
 // (hi x, y, z and the packed lo of lo_encode; u = hi + lo).
-// PB (P B0): the D x D entries of a particle, row-major, in pb_chunks
-// 16-byte chunks; chunk c of all particles forms one dense array, chunk c of
-// particle j at 16-byte index c n + j.  A neighbour gather then reads one
-// 16-byte vector from each of a few dense arrays, so a warp's gathers touch
-// fewer cache lines than with a padded record per particle.
+// PB (P B0): the D x D entries of a particle, row-major, in pb_full whole
+// 16-byte chunks and pb_tail leftover entries; chunk c of all particles forms
+// one dense array (chunk c of particle j at 16-byte index c n + j), each
+// leftover entry another.  A neighbour gather then reads one 16-byte vector
+// from each of a few dense arrays and one scalar for the leftover, so a
+// warp's gathers touch fewer cache lines than with a padded record per
+// particle (36 bytes per FP32 3D neighbour instead of 48).
 template <typename T, int D>
 struct PBL {
-    static constexpr int C = pb_chunks(sizeof(T), D);
+    static constexpr int C = pb_full(sizeof(T), D);
+    static constexpr int TL = pb_tail(sizeof(T), D);
     static constexpr int E = 16 / (int)sizeof(T);  // entries per chunk
     __device__ static void load(const T* p, int n, int j, T (&m)[D][D])
     {
-        T e[C * E];
+        T e[C * E + TL];
+#pragma unroll
+        for (int t = 0; t < TL; ++t) e[C * E + t] = __ldg(p + (size_t)(C * E + t) * n + j);
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
@@ -67,9 +72,11 @@ struct PBL {
     }
     __device__ static void store(T* p, int n, int j, const T (&m)[D][D])
     {
-        T e[C * E];
+        T e[C * E + TL];
 #pragma unroll
-        for (int k = 0; k < C * E; ++k) e[k] = k < D * D ? m[k / D][k % D] : T(0);
+        for (int k = 0; k < C * E + TL; ++k) e[k] = m[k / D][k % D];
+#pragma unroll
+        for (int t = 0; t < TL; ++t) p[(size_t)(C * E + t) * n + j] = e[C * E + t];
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
             for (int c = 0; c < C; ++c)

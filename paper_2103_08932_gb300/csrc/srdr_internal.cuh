@@ -12,7 +12,8 @@
 //   v     T [n][4] velocity records (vx, vy, vz, 1/m): one 16-byte (FP32) or
 //         two 16-byte (FP64) accesses per particle
 //   B0    T [D*D][n] row-major tensor components, SoA (read by the owner only)
-//   PB    T [pb_chunks][n] 16-byte chunks of the row-major entries (gathered)
+//   PB    T [pb_full][n] 16-byte chunks of the row-major entries, then
+//         [pb_tail][n] leftover entries (gathered)
 //   G     T [3][n]   sum_j V_j grad W_ij (for the difference form of the force)
 //   CSR   row_ptr int32 [n+1], col int32 [nnz] (sorted ids, ascending),
 //         loc uint16 [nnz] (index of j inside the 3^d-cell footprint of
@@ -127,7 +128,7 @@ struct StepArgs {
     const T* __restrict__ cpos;   // [n][4] offset in its cell (x, y, z) and volume
     const int* __restrict__ ccell; // [n] packed cell coordinates x | y << 10 | z << 20
     const T* __restrict__ B0;   // [D*D][n]
-    T* __restrict__ PB;         // [pb_chunks][n] 16-byte chunks
+    T* __restrict__ PB;         // [pb_full][n] 16-byte chunks, [pb_tail][n] entries
     const T* __restrict__ Gs;   // [3][n]
     const T* __restrict__ dvisc; // [n][4] explicit comparator: dt a_visc(v^n), else null
     const T* __restrict__ bf;    // [n][4] per-particle body force (twist), else null
@@ -297,15 +298,24 @@ inline double kernel_kc(int dim, double h)
 __host__ __device__ inline int flow_epoch_word(int ncells) { return (ncells + 31) & ~31; }
 __host__ __device__ inline int flow_words(int ncells) { return flow_epoch_word(ncells) + 64; }
 
-// elements per particle of the AoS P B0 array (whole 16-byte vectors)
-// 16-byte chunks holding the dim x dim entries of one P B0 (FP32 3D: 3,
-// FP64 3D: 5, 2D: 1 or 2)
+// P B0 layout: the dim x dim entries of a particle, row-major, as pb_full
+// whole 16-byte chunks (FP32 3D: 2, FP64 3D: 4, FP32 2D: 1, FP64 2D: 2) and
+// pb_tail leftover entries (3D: 1, 2D: 0).  Chunk c of all particles is one
+// dense array (chunk c of particle j at 16-byte index c n + j); leftover
+// entry t of particle j sits at T index (pb_full E + t) n + j, E = 16 / T.
+__host__ __device__ constexpr int pb_full(size_t tsize, int dim) { return (int)(dim * dim * tsize / 16); }
+__host__ __device__ constexpr int pb_tail(size_t tsize, int dim)
+{
+    return dim * dim - pb_full(tsize, dim) * (int)(16 / tsize);
+}
+// 16-byte chunks covering one particle's entries (a padded record in the
+// brick-tiled passes' shared memory: FP32 3D: 3, FP64 3D: 5, 2D: 1 or 2)
 __host__ __device__ constexpr int pb_chunks(size_t tsize, int dim)
 {
     return (int)((dim * dim * tsize + 15) / 16);
 }
 // T elements per particle in PB
-inline int pb_stride(size_t tsize, int dim) { return pb_chunks(tsize, dim) * (int)(16 / tsize); }
+inline int pb_stride(size_t tsize, int dim) { return pb_full(tsize, dim) * (int)(16 / tsize) + pb_tail(tsize, dim); }
 
 // setup (setup.cu)
 srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* vol,

@@ -35,17 +35,26 @@ __device__ inline void cp_async16(void* dst, const void* src)
 }
 __device__ inline void cp_async_wait_all_t() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// halo copy of P B0: record h of the block's halo (chunks x 16 bytes) <-
-// chunks c = 0..chunks-1 of particle halo[h] (chunk c of particle j at
-// 16-byte index c n + j of src)
-__device__ inline void stage_halo_pb(unsigned char* dst, const unsigned char* src, int n,
-                                     const int* __restrict__ halo, int nh, int chunks)
+// halo copy of P B0: record h of the block's halo (pb_chunks x 16 bytes,
+// entries in row-major order) <- the pb_full whole chunks of particle
+// halo[h] (chunk c of particle j at 16-byte index c n + j of src) and its
+// pb_tail leftover entries (entry t at T index (pb_full E + t) n + j)
+template <typename T, int D>
+__device__ inline void stage_halo_pb(unsigned char* dst, const T* src, int n, const int* __restrict__ halo,
+                                     int nh)
 {
-    const int nchunks = nh * chunks;
-    for (int q = threadIdx.x; q < nchunks; q += blockDim.x) {
-        const int h = q / chunks, c = q - h * chunks;
+    constexpr int C = pb_chunks(sizeof(T), D), F = pb_full(sizeof(T), D), TL = pb_tail(sizeof(T), D);
+    constexpr int E = 16 / (int)sizeof(T);
+    constexpr int K = F + TL;  // copies per halo particle
+    const unsigned char* sb = reinterpret_cast<const unsigned char*>(src);
+    for (int q = threadIdx.x; q < nh * K; q += blockDim.x) {
+        const int h = q / K, c = q - h * K;
         const int j = __ldg(halo + h);
-        cp_async16(dst + ((size_t)h * chunks + c) * 16, src + ((size_t)c * n + j) * 16);
+        if (c < F)
+            cp_async16(dst + ((size_t)h * C + c) * 16, sb + ((size_t)c * n + j) * 16);
+        else
+            cp_async_t<T>(reinterpret_cast<T*>(dst + (size_t)h * C * 16) + F * E + (c - F),
+                          src + (size_t)(F * E + c - F) * n + j);
     }
     cp_async_wait_all_t();
     __syncthreads();
@@ -176,8 +185,7 @@ __global__ void __launch_bounds__(kTileThreads) k_pass_b_tiled(StepArgs<T> a, Ti
     if (a.dflag) final_step = *a.dflag == 0;
     extern __shared__ __align__(16) unsigned char tsm[];
     const BrickInfo bi = tl.info[blockIdx.x];
-    stage_halo_pb(tsm, reinterpret_cast<const unsigned char*>(a.PB), a.n, tl.halo + bi.halo_base, bi.nhalo,
-                  pb_chunks(sizeof(T), D));
+    stage_halo_pb<T, D>(tsm, a.PB, a.n, tl.halo + bi.halo_base, bi.nhalo);
     const T* spb = reinterpret_cast<const T*>(tsm);
     const int lane = threadIdx.x & 31;
     for (int k0 = 0; k0 < bi.nown; k0 += blockDim.x) {
