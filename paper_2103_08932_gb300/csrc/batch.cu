@@ -8,8 +8,10 @@
 //   k_batch_pass_a   stress pass over all slices of all active bodies
 //   k_batch_pass_b   force pass, v* = v^n + dt a
 //   k_batch_sweep    S_d of every damped body, all colours forward then
-//                    backward, colour-synchronised across the whole batch in
-//                    one cooperative launch (Sec. 3.4)
+//                    backward in one cooperative launch (Sec. 3.4), either
+//                    with grid barriers between colour phases or, in
+//                    k_batch_sweep_flow, with each cell waiting only for the
+//                    overlapping cells of its own body
 //   k_batch_finish   constraints, displacement update, KE slice partials
 //   k_batch_ke       per-body FP64 KE, KE_max, retirement test
 // The per-particle arithmetic is the single-body code (passes.cuh,
@@ -44,6 +46,8 @@ struct BatchEntry {
     double alpha;
     unsigned long long seed;
     int nslices;
+    int ncells_nonempty;
+    unsigned* flow;  // the body's cell-wise synchronisation words
 };
 
 // one block: damping decision of every body; any[0] = some body is damped
@@ -212,6 +216,76 @@ __global__ void __launch_bounds__(32) k_batch_sweep(const BatchEntry<T>* __restr
     cp_async_wait_all();
 }
 
+// The batched S_d with cell-wise waits instead of grid barriers (the
+// single-body k_sweep_flow, per body): before each of its phases a cell
+// waits for the cells of its own body whose footprints overlap its own to
+// have finished their earlier phases.  The cell that finishes its body's
+// last direction advances the body's epoch.  Same parameters as
+// k_batch_sweep (bar unused) and bitwise the same results.
+template <typename T, int D, int G>
+__global__ void __launch_bounds__(32) k_batch_sweep_flow(const BatchEntry<T>* __restrict__ tab,
+                                                         const int2* __restrict__ cells,
+                                                         const int* __restrict__ colour_ptr, int ncolours,
+                                                         const int* __restrict__ damp,
+                                                         const int* __restrict__ any, unsigned* bar,
+                                                         DevScalars* status, int F, int P, int C)
+{
+    constexpr int L = 32 / G;
+    (void)bar;
+    if (!*(volatile const int*)any) return;
+    if (*(volatile int*)&status->status == DEV_TIMEOUT) return;  // words left mid-sweep: host resets them
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / L, gl = threadIdx.x % L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
+    const CellSmem<T, D> s =
+        cell_smem<T, D>(smem_raw + (size_t)g * cell_smem_bytes<T, D>(F, P, C), F, P, C);
+    const int q0 = blockIdx.x * G + g, qs = gridDim.x * G;
+    int sph = 0;
+    const int clast = last_colour(colour_ptr, ncolours);
+    int staged = batch_next(cells, damp, colour_ptr, ncolours, clast, 0, -1, q0, qs, &sph);
+    CellStage st{};
+    if (staged >= 0) {
+        const int2 e = cells[staged];
+        st = stage_cell<T, D, L>(tab[e.x].sweep, e.y, s, gl, gmask);
+    }
+    bool ok = true;
+    for (int ph = 0; ph < 2 * ncolours && ok; ++ph) {
+        const int backward = ph >= ncolours;
+        const int col = backward ? 2 * ncolours - 1 - ph : ph;
+        const int c0 = __ldg(colour_ptr + col), c1 = __ldg(colour_ptr + col + 1);
+        if (c1 == c0 || (backward && col == clast)) continue;
+        const int mode = col == clast ? 2 : backward;
+        while (staged >= 0 && sph == ph) {
+            const int2 e = cells[staged];
+            const SweepArgs<T>& a = tab[e.x].sweep;
+            unsigned* flow = tab[e.x].flow;
+            const int fo = flow_epoch_word(a.nx * a.ny * a.nz);
+            const unsigned epoch = *(volatile const unsigned*)(flow + fo);
+            if (!flow_wait<T, L>(a, flow, epoch, e.y, ph, ncolours, clast, status, gl, gmask)) {
+                ok = false;
+                break;
+            }
+            run_cell<T, D, L>(a, st, mode, s, gl, gmask);
+            if (gl == 0) {
+                __threadfence();  // the group's write-back (ordered by run_cell's __syncwarp) first
+                atomicAdd(flow + e.y, mode == 2 ? 2u : 1u);
+                // the body's last cell to finish its last direction ends the body's sweep
+                if (mode != 0 && atomicAdd(flow + fo + 32, 1u) == (unsigned)tab[e.x].ncells_nonempty - 1u) {
+                    atomicExch(flow + fo + 32, 0u);
+                    __threadfence();
+                    atomicAdd(flow + fo, 1u);
+                }
+            }
+            staged = batch_next(cells, damp, colour_ptr, ncolours, clast, ph, staged, q0, qs, &sph);
+            if (staged >= 0) {
+                const int2 e2 = cells[staged];
+                st = stage_cell<T, D, L>(tab[e2.x].sweep, e2.y, s, gl, gmask);
+            }
+        }
+    }
+    cp_async_wait_all();  // no copy may land after the group has left
+}
+
 __global__ void k_batch_set_tol(DevScalars* const* scs, int nb, double tol)
 {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
@@ -240,6 +314,7 @@ struct srdr_batch {
     int prec = SRDR_FP64, dim = 3, ncolours = 27;
     int F = 0, P = 0, C = 0;
     int G = 2;            // sweep cells per warp
+    int cellwise = 1;     // sweep synchronised by cell-wise waits (1) or grid barriers (0)
     int pass_threads = 256;
     int tuned = 0;
     // device
@@ -342,6 +417,8 @@ srdr_status upload_table(srdr_batch* bt)
         tab[k].alpha = b->desc.alpha;
         tab[k].seed = b->desc.seed;
         tab[k].nslices = b->nslices;
+        tab[k].ncells_nonempty = b->ncells_nonempty;
+        tab[k].flow = b->flow;
     }
     if (!bt->tab) SRDR_TRY(balloc(bt, &bt->tab, sizeof(BatchEntry<T>) * (size_t)nb));
     SRDR_CK(cudaMemcpyAsync(bt->tab, tab.data(), sizeof(BatchEntry<T>) * (size_t)nb,
@@ -407,13 +484,13 @@ srdr_status sweep_config_g(srdr_batch* bt, const void** fn)
         set_error("batched sweep needs %zu bytes of shared memory per block", smem);
         return SRDR_ERR_INVALID;
     }
-    *fn = (const void*)k_batch_sweep<T, D, G>;
+    *fn = bt->cellwise ? (const void*)k_batch_sweep_flow<T, D, G> : (const void*)k_batch_sweep<T, D, G>;
     if (smem > 48 * 1024)
         SRDR_CK(cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, nsm = 0;
     SRDR_CK(cudaGetDevice(&dev));
     SRDR_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    SRDR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_sweep<T, D, G>, 32, smem));
+    SRDR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, *fn, 32, smem));
     if (per_sm < 1) {
         set_error("batched sweep kernel does not fit on an SM");
         return SRDR_ERR_INVALID;
@@ -518,12 +595,18 @@ srdr_status run_chunk(srdr_batch* bt, int64_t nsteps)
 
 // Autotuner: on fresh bodies (v = 0, where the sweep leaves every velocity
 // at exactly 0 and the stress pass only rewrites P B0) time the sweep with
-// 1, 2, 4 cells per warp and the stress pass with 128, 256, 512 threads per
-// block, and keep the fastest.  Bodies that already moved keep the defaults.
+// 1, 2, 4 cells per warp, with cell-wise waits and with grid barriers, and
+// the stress pass with 128, 256, 512 threads per block, and keep the
+// fastest.  Bodies that already moved keep the defaults.  When every body
+// asks for the same synchronisation (srdr_body_sweep_sync), the batch uses it.
 template <typename T, int D>
 srdr_status autotune(srdr_batch* bt)
 {
     bt->tuned = 1;
+    int want = bt->bodies.empty() ? SRDR_SWEEP_AUTO : bt->bodies[0]->sweep_sync;
+    for (srdr_body* b : bt->bodies)
+        if (b->sweep_sync != want) want = SRDR_SWEEP_AUTO;
+    if (want != SRDR_SWEEP_AUTO) bt->cellwise = want == SRDR_SWEEP_CELLS;
     for (srdr_body* b : bt->bodies)
         if (b->step != 0) return SRDR_OK;
     const BatchEntry<T>* tab = static_cast<const BatchEntry<T>*>(bt->tab);
@@ -556,22 +639,27 @@ srdr_status autotune(srdr_batch* bt)
     int F = bt->F, P = bt->P, C = bt->C;
     void* sweep_params[] = {&tab, &cells, &cptr, &ncol, &damp, &any, &bar, &status, &F, &P, &C};
     float best = 3.0e38f;
-    int best_g = bt->G;
-    for (int g : {1, 2, 4}) {
-        bt->G = g;
-        const void* fn = nullptr;
-        if (sweep_config<T, D>(bt, &fn) != SRDR_OK) continue;
-        float ms = 0;
-        SRDR_TRY(timed([&] {
-            cudaLaunchCooperativeKernel(fn, dim3(bt->sweep_grid), dim3(32), sweep_params, bt->sweep_smem,
-                                        bt->stream);
-        }, &ms));
-        if (ms < best) {
-            best = ms;
-            best_g = g;
+    int best_g = bt->G, best_c = bt->cellwise;
+    for (int cw : {1, 0})
+        for (int g : {1, 2, 4}) {
+            if (want != SRDR_SWEEP_AUTO && cw != (want == SRDR_SWEEP_CELLS)) continue;
+            bt->G = g;
+            bt->cellwise = cw;
+            const void* fn = nullptr;
+            if (sweep_config<T, D>(bt, &fn) != SRDR_OK) continue;
+            float ms = 0;
+            SRDR_TRY(timed([&] {
+                cudaLaunchCooperativeKernel(fn, dim3(bt->sweep_grid), dim3(32), sweep_params, bt->sweep_smem,
+                                            bt->stream);
+            }, &ms));
+            if (ms < best) {
+                best = ms;
+                best_g = g;
+                best_c = cw;
+            }
         }
-    }
     bt->G = best_g;
+    bt->cellwise = best_c;
     best = 3.0e38f;
     int best_t = bt->pass_threads;
     // the block size must fit the register use of both passes (FP64 3D uses
@@ -630,6 +718,8 @@ srdr_status batch_steps(srdr_batch* bt, int64_t nsteps, double tol, int64_t chec
             // the barrier words are left mid-sweep: reset them and the status
             DevScalars z{};
             SRDR_CK(cudaMemsetAsync(bt->bar, 0, kBarWords * sizeof(unsigned), bt->stream));
+            for (srdr_body* b : bt->bodies)
+                SRDR_CK(cudaMemsetAsync(b->flow, 0, sizeof(unsigned) * flow_words(b->ncells), bt->stream));
             SRDR_CK(cudaMemcpyAsync(bt->status, &z, sizeof(z), cudaMemcpyHostToDevice, bt->stream));
             SRDR_CK(cudaStreamSynchronize(bt->stream));
             set_error("batched damping sweep: a grid barrier timed out");

@@ -614,18 +614,19 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
 // (cooperative launch), so the lowest unfinished phase always progresses.
 //
 // flow buffer (unsigned, zeroed at creation): done[c] for every cell of the
-// grid (phases finished, counted over all sweeps), then at word
-// fo = ncells rounded up to 32 the epoch (sweeps finished), and at fo + 32
-// the number of groups that have finished this sweep; the last of them
-// advances the epoch.  After e sweeps done[c] = e for cells of the last
-// colour (one fused phase) and 2 e for the others.
+// grid (sweep directions finished, counted over all sweeps: the fused phase
+// of the last colour counts both), then at word fo = ncells rounded up to 32
+// the epoch (sweeps finished), and at fo + 32 a count of finishers of this
+// sweep, the last of which advances the epoch (the groups of a single-body
+// sweep; the cells of the body in a batched sweep).  After e sweeps
+// done[c] = 2 e for every cell, whichever colour a launch fuses.
 
-// phases of a cell of colour cy that come before phase ph
+// directions of a cell of colour cy finished before phase ph (the colour
+// clast runs both in its forward phase)
 __device__ inline unsigned phases_before(int cy, int ph, int ncolours, int clast)
 {
-    unsigned k = cy < ph ? 1u : 0u;
-    if (cy != clast && 2 * ncolours - 1 - cy < ph) ++k;
-    return k;
+    if (cy == clast) return cy < ph ? 2u : 0u;
+    return (cy < ph ? 1u : 0u) + (2 * ncolours - 1 - cy < ph ? 1u : 0u);
 }
 
 // Wait until the neighbourhood of cell c is ready for its phase ph.  Each
@@ -633,7 +634,7 @@ __device__ inline unsigned phases_before(int cy, int ph, int ncolours, int clast
 // second (DEV_TIMEOUT) or when another group has already given up.
 template <typename T, int L>
 __device__ inline bool flow_wait(const SweepArgs<T>& a, const unsigned* done, unsigned epoch, int c, int ph,
-                                 int ncolours, int clast, int gl, unsigned gmask)
+                                 int ncolours, int clast, DevScalars* status, int gl, unsigned gmask)
 {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
@@ -646,18 +647,18 @@ __device__ inline bool flow_wait(const SweepArgs<T>& a, const unsigned* done, un
         const int d = x + nx * (y + ny * z);
         if (__ldg(a.cell_start + d + 1) == __ldg(a.cell_start + d)) continue;  // empty: never runs
         const int col = x % 3 + 3 * (y % 3) + 9 * (z % 3);
-        const unsigned need = epoch * (col == clast ? 1u : 2u) + phases_before(col, ph, ncolours, clast);
+        const unsigned need = 2u * epoch + phases_before(col, ph, ncolours, clast);
         long long polls = 0;
         unsigned long long t0 = 0;
         while (*(volatile const unsigned*)(done + d) < need) {
             if (polls == 0) t0 = global_ns();
             if ((++polls & 63) == 0) {
-                if (*(volatile int*)&a.sc->status != DEV_OK) {
+                if (*(volatile int*)&status->status != DEV_OK) {
                     ok = false;
                     break;
                 }
                 if (global_ns() - t0 > kWaitNs || polls > kWaitPolls) {
-                    atomicCAS(&a.sc->status, DEV_OK, DEV_TIMEOUT);
+                    atomicCAS(&status->status, DEV_OK, DEV_TIMEOUT);
                     ok = false;
                     break;
                 }
@@ -702,14 +703,14 @@ __global__ void __launch_bounds__(32 * W) k_sweep_flow(SweepArgs<T> a, const int
         for (int cid = c0 + q0; cid < c1; cid += qs) {
             // staged == cid here: items are visited in the order next_item gives
             const int cell = __ldg(a.colour_cells + cid);
-            if (!flow_wait<T, L>(a, done, epoch, cell, ph, ncolours, clast, gl, gmask)) {
+            if (!flow_wait<T, L>(a, done, epoch, cell, ph, ncolours, clast, a.sc, gl, gmask)) {
                 ok = false;
                 break;
             }
             run_cell<T, D, L>(a, st, mode, s, gl, gmask);
             if (gl == 0) {
                 __threadfence();  // the group's write-back (ordered by run_cell's __syncwarp) first
-                atomicAdd(done + cell, 1u);
+                atomicAdd(done + cell, mode == 2 ? 2u : 1u);
             }
             staged = next_item(colour_ptr, ncolours, clast, ph, cid, q0, qs);
             if (staged >= 0) st = stage_cell<T, D, L>(a, __ldg(a.colour_cells + staged), s, gl, gmask);

@@ -42,25 +42,36 @@ def uneven_specs(dim=3):
     ]
 
 
-@pytest.mark.parametrize("dim,precision", [(3, srdr.SRDR_FP64), (3, srdr.SRDR_FP32_MIXED),
-                                           (2, srdr.SRDR_FP64)])
-def test_batch_steps_equal_single_bodies(dim, precision):
+@pytest.mark.parametrize("dim,precision,sync", [
+    (3, srdr.SRDR_FP64, srdr.SRDR_SWEEP_AUTO), (3, srdr.SRDR_FP32_MIXED, srdr.SRDR_SWEEP_AUTO),
+    (2, srdr.SRDR_FP64, srdr.SRDR_SWEEP_AUTO), (3, srdr.SRDR_FP32_MIXED, srdr.SRDR_SWEEP_CELLS),
+    (3, srdr.SRDR_FP64, srdr.SRDR_SWEEP_BARRIER), (2, srdr.SRDR_FP32_MIXED, srdr.SRDR_SWEEP_CELLS)])
+def test_batch_steps_equal_single_bodies(dim, precision, sync):
+    """Batched steps (barrier or cell-wise batched sweep) equal the same
+    bodies stepped alone (cell-wise or barrier single-body sweep) bit for bit;
+    the bodies then keep stepping alone and still agree."""
     specs = uneven_specs(dim)
     single = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
     for b in single:
+        b.sweep_sync(srdr.SRDR_SWEEP_BARRIER if sync == srdr.SRDR_SWEEP_CELLS else srdr.SRDR_SWEEP_CELLS)
         b.step(40)
     bodies = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
+    for b in bodies:
+        b.sweep_sync(sync)
     batch = srdr.Batch(bodies)
     batch.step(40)
+    info = batch.info()
+    assert info["sweep_cells_per_warp"] in (1, 2, 4) and info["pass_threads"] in (128, 256, 512)
+    batch.close()
+    for a, b in zip(single, bodies):
+        a.step(25)
+        b.step(25)  # alone after the batch: the cell-wise counts carry over
     for a, b in zip(single, bodies):
         assert np.array_equal(a.velocity(), b.velocity())
         assert np.array_equal(a.displacement(), b.displacement())
         sa, sb = a.stats(), b.stats()
         assert sa["damped_steps"] == sb["damped_steps"] > 0
         assert sa["ke"] == sb["ke"]
-    info = batch.info()
-    assert info["sweep_cells_per_warp"] in (1, 2, 4) and info["pass_threads"] in (128, 256, 512)
-    batch.close()
 
 
 def test_batch_relax_retires_each_body_at_its_own_step():
