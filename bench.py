@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sweep-sync", choices=["auto", "barrier", "cells"], default="auto",
+                    help="synchronisation of the damping sweep's colour phases (default: autotuned)")
     ap.add_argument("--workload", choices=["plate", "batched", "served", "block", "compare"],
                     default="plate")
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
@@ -237,6 +239,7 @@ def run_gpu(args):
     desc = srdr.make_desc(spec, precision=srdr.SRDR_FP32_MIXED)
     stream = torch.cuda.current_stream()
     body = srdr.Body(desc, stream=stream.cuda_stream)
+    body.sweep_sync(SYNC_MODES[args.sweep_sync])
 
     body.step(args.warmup)
     torch.cuda.synchronize()
@@ -298,6 +301,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2 = srdr.Body(desc, r0=r0p.numpy(), flags=flp.numpy(), stream=stream.cuda_stream)
+        b2.sweep_sync(SYNC_MODES[args.sweep_sync])
         b2.step(args.steps)
         import ctypes
         srdr._check(srdr.lib().srdr_body_read_displacement(
@@ -343,7 +347,10 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def run_batched(nbodies, n_lo, n_hi, steps, seed=3):
+SYNC_MODES = {"auto": 0, "barrier": 1, "cells": 2}
+
+
+def run_batched(nbodies, n_lo, n_hi, steps, seed=3, sync="auto"):
     """Uneven bodies (counts log-uniform in [n_lo, n_hi], box / beam / plate,
     aspect 1-20, E log-uniform 1e5-1e7, nu 0.2-0.45, gravity or end load):
     `steps` steps of all of them as one batch vs the same steps one body at a
@@ -355,6 +362,8 @@ def run_batched(nbodies, n_lo, n_hi, steps, seed=3):
     specs = S.random_bodies(nbodies, n_lo, n_hi, seed)
     descs = [srdr.make_desc(s, precision=srdr.SRDR_FP32_MIXED) for s in specs]
     bodies = [srdr.Body(d) for d in descs]
+    for b in bodies:
+        b.sweep_sync(SYNC_MODES[sync])
     n_total = sum(b.n for b in bodies)
     batch = srdr.Batch(bodies)
     batch.step(8)  # warm-up, autotuner, graph capture
@@ -496,7 +505,7 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
-        print(json.dumps({"impl": "gpu", "batched": run_batched(256, 1e3, 2e5, args.steps)}))
+        print(json.dumps({"impl": "gpu", "batched": run_batched(256, 1e3, 2e5, args.steps, sync=args.sweep_sync)}))
     elif args.workload == "block":
         print(json.dumps({"impl": "gpu", "block": run_block(args.steps)}))
     elif args.workload == "compare":

@@ -594,7 +594,8 @@ srdr_status run_chunk(srdr_batch* bt, int64_t nsteps)
 }
 
 // Autotuner: on fresh bodies (v = 0, where the sweep leaves every velocity
-// at exactly 0 and the stress pass only rewrites P B0) time the sweep with
+// at exactly 0 and the stress pass only rewrites P B0) time the sweep (on
+// the bodies the first step damps) with
 // 1, 2, 4 cells per warp, with cell-wise waits and with grid barriers, and
 // the stress pass with 128, 256, 512 threads per block, and keep the
 // fastest.  Bodies that already moved keep the defaults.  When every body
@@ -611,10 +612,19 @@ srdr_status autotune(srdr_batch* bt)
         if (b->step != 0) return SRDR_OK;
     const BatchEntry<T>* tab = static_cast<const BatchEntry<T>*>(bt->tab);
     const int nb = (int)bt->bodies.size();
-    std::vector<int> ones(nb, 1);
-    int one = 1;
-    SRDR_CK(cudaMemcpyAsync(bt->damp, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, bt->stream));
-    SRDR_CK(cudaMemcpyAsync(bt->any, &one, sizeof(int), cudaMemcpyHostToDevice, bt->stream));
+    // the sweep is timed on the bodies the first step's random choice damps
+    // (the share of damped bodies decides between cell-wise waits and grid
+    // barriers), or on all of them when it damps none
+    k_batch_decide<T><<<1, 1024, 0, bt->stream>>>(tab, nb, bt->damp, bt->any);
+    int any_h = 0;
+    SRDR_CK(cudaMemcpyAsync(&any_h, bt->any, sizeof(int), cudaMemcpyDeviceToHost, bt->stream));
+    SRDR_CK(cudaStreamSynchronize(bt->stream));
+    if (!any_h) {
+        std::vector<int> ones(nb, 1);
+        int one = 1;
+        SRDR_CK(cudaMemcpyAsync(bt->damp, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, bt->stream));
+        SRDR_CK(cudaMemcpyAsync(bt->any, &one, sizeof(int), cudaMemcpyHostToDevice, bt->stream));
+    }
     cudaEvent_t e0, e1;
     SRDR_CK(cudaEventCreate(&e0));
     SRDR_CK(cudaEventCreate(&e1));
