@@ -221,9 +221,12 @@ srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp, int sweep_
  * for the cells whose footprints overlap its own (within 2 cells on every
  * axis) to have finished their earlier phases, so the order of every pair of
  * cells that interact is the canonical one.  SRDR_SWEEP_AUTO (the default):
- * the autotuner times both with the cells-per-warp choices of
- * srdr_body_tune (which must then be left to the autotuner for AUTO to take
- * effect; a fixed mapping uses SRDR_SWEEP_CELLS unless BARRIER is asked).
+ * the autotuner times cell-wise waits with one cell per warp and grid
+ * barriers with one or two (with more cells per warp, a warp's groups would
+ * take turns: one polling while the other's chain waits); a mapping fixed by
+ * srdr_body_tune uses cell-wise waits for one cell per warp and grid
+ * barriers otherwise.  A batch uses the mode all of its bodies ask for, else
+ * its own autotuner's choice.
  * Results are bitwise the same under every choice.  Every wait is bounded
  * (one second); a sweep whose wait runs out sets the body's status, and
  * srdr_body_relax returns SRDR_ERR_TIMEOUT after resetting the

@@ -611,7 +611,9 @@ srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp, int warps_per_block
         b->sweep_tuned = 1;
         b->sweep_cells_per_warp = cells_per_warp;
         b->sweep_warps_per_block = warps_per_block;
-        b->sweep_cellwise = b->sweep_sync != SRDR_SWEEP_BARRIER;
+        // cell-wise waits pair with one cell per warp unless asked for
+        b->sweep_cellwise = b->sweep_sync == SRDR_SWEEP_CELLS ||
+                            (b->sweep_sync == SRDR_SWEEP_AUTO && cells_per_warp == 1);
     }
     return SRDR_OK;
 }

@@ -313,7 +313,7 @@ struct srdr_batch {
     cudaStream_t stream = nullptr;
     int prec = SRDR_FP64, dim = 3, ncolours = 27;
     int F = 0, P = 0, C = 0;
-    int G = 2;            // sweep cells per warp
+    int G = 1;            // sweep cells per warp
     int cellwise = 1;     // sweep synchronised by cell-wise waits (1) or grid barriers (0)
     int pass_threads = 256;
     int tuned = 0;
@@ -653,6 +653,9 @@ srdr_status autotune(srdr_batch* bt)
     for (int cw : {1, 0})
         for (int g : {1, 2, 4}) {
             if (want != SRDR_SWEEP_AUTO && cw != (want == SRDR_SWEEP_CELLS)) continue;
+            // cell-wise waits with one cell per warp only: two groups of a
+            // warp would take turns, one polling while the other's chain waits
+            if (cw && g > 1) continue;
             bt->G = g;
             bt->cellwise = cw;
             const void* fn = nullptr;
@@ -932,6 +935,30 @@ srdr_status srdr_batch_info(const srdr_batch* bt, int64_t* steps, int64_t* launc
 }
 
 void srdr_batch_destroy(srdr_batch* bt) { batch_free(bt); }
+
+}  // extern "C"
+
+namespace srdr {
+// launch configuration of a tuned batch, carried over to the next batch of
+// a continuous-batching loop (whose bodies have moved, so it cannot tune)
+void batch_get_tuning(const srdr_batch* bt, int cfg[4])
+{
+    cfg[0] = bt->tuned;
+    cfg[1] = bt->G;
+    cfg[2] = bt->cellwise;
+    cfg[3] = bt->pass_threads;
+}
+void batch_set_tuning(srdr_batch* bt, const int cfg[4])
+{
+    if (!cfg[0]) return;
+    bt->tuned = 1;
+    bt->G = cfg[1];
+    bt->cellwise = cfg[2];
+    bt->pass_threads = cfg[3];
+}
+}  // namespace srdr
+
+extern "C" {
 
 srdr_status srdr_desc_particle_count(const srdr_body_desc* d, int64_t* n)
 {

@@ -128,6 +128,7 @@ void worker_main(srdr_server* s)
     std::vector<Live> live;
     srdr_batch* batch = nullptr;
     bool dirty = true;
+    int tuning[4] = {0, 0, 0, 0};  // the tuned launch configuration, once a batch has one
     for (;;) {
         // admission: slots and device-memory budget
         std::vector<Request> take;
@@ -161,7 +162,14 @@ void worker_main(srdr_server* s)
             s->peak_live = std::max(s->peak_live, (int)live.size());
         }
         if (dirty) {
-            if (batch) srdr_batch_destroy(batch);
+            // the new batch keeps the launch configuration the first batch
+            // tuned (its bodies have moved, so it cannot tune itself)
+            if (batch) {
+                int cfg[4];
+                srdr::batch_get_tuning(batch, cfg);
+                if (cfg[0]) std::copy(cfg, cfg + 4, tuning);
+                srdr_batch_destroy(batch);
+            }
             batch = nullptr;
             std::vector<srdr_body*> bodies;
             for (Live& l : live) bodies.push_back(l.body);
@@ -172,6 +180,7 @@ void worker_main(srdr_server* s)
                 batch = nullptr;
                 continue;
             }
+            srdr::batch_set_tuning(batch, tuning);
             dirty = false;
         }
         // one chunk of batched steps; every body stops at its own criterion

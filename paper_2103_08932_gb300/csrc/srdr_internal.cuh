@@ -276,6 +276,10 @@ struct srdr_body {
 namespace srdr {
 
 srdr_status dev_alloc(srdr_body* b, void** p, size_t bytes);
+// a tuned batch's launch configuration (batch.cu), for the next batch of a
+// continuous-batching loop: {tuned, cells per warp, cell-wise, pass threads}
+void batch_get_tuning(const srdr_batch* bt, int cfg[4]);
+void batch_set_tuning(srdr_batch* bt, const int cfg[4]);
 srdr_status dev_free(srdr_body* b, void* p);
 template <typename P>
 inline srdr_status dalloc(srdr_body* b, P** p, size_t count)

@@ -167,6 +167,9 @@ srdr_status autotune_sweep(srdr_body* b)
         for (int w : {1, 4}) {
             if ((cw && b->sweep_sync == SRDR_SWEEP_BARRIER) || (!cw && b->sweep_sync == SRDR_SWEEP_CELLS))
                 continue;
+            // cell-wise waits with one cell per warp only: two groups of a
+            // warp would take turns, one polling while the other's chain waits
+            if (cw && g > 1) continue;
             b->sweep_cellwise = cw;
             b->sweep_cells_per_warp = g;
             b->sweep_warps_per_block = w;
