@@ -197,7 +197,10 @@ srdr_status srdr_body_read_field(const srdr_body* body, int field, double* host_
  * k = 0 stops.  srdr_body_kernel_times synchronises and returns the
  * accumulated device milliseconds and timed intervals per class and the
  * launches of all steps since the profile call.  Profiled stepping launches
- * every step directly (no graph replay). */
+ * every step directly (no graph replay).  The kinetic-energy reduction is
+ * part of the force pass (undamped step) or of the finish pass (damped step)
+ * on the sliced-ELL mapping; SRDR_K_KE times the separate KE kernels of the
+ * brick-tiled mapping. */
 enum { SRDR_K_PASS_A = 0, SRDR_K_PASS_B = 1, SRDR_K_SWEEP = 2, SRDR_K_FINISH = 3, SRDR_K_KE = 4,
        SRDR_K_NCLASS = 5 };
 typedef struct {

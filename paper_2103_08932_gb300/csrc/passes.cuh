@@ -362,28 +362,32 @@ __device__ inline void slice_partial_store(double x, double* out, int i, int n)
     if ((threadIdx.x & 31) == 0 && (slice << 5) < n) out[slice] = x;
 }
 
-// One block of kThreads: FP64 KE of one body from its slice partials in a
-// fixed order, its running maximum, the step counters and the relax test.
 // threads of the one-block kinetic-energy reductions (single body and batch
-// use the same count, so a body's KE has the same bits in both)
+// use the same count, so a body's KE has the same bits in both); the block
+// also updates the running maximum, the step counters and the relax test
 constexpr int kKeThreads = 256;
 
-__device__ inline void ke_finalize(const double* __restrict__ part, int np, DevScalars* sc,
-                                   int damped)
+// The body's FP64 kinetic energy in one fixed order, whichever kernels
+// produced its parts.  The slice partials (32 particles each) form groups of
+// kKeGroup consecutive slices, each summed in slice order; thread t of the
+// kKeThreads adds groups t, t + B, ... in order; a warp butterfly and
+// thread 0's sum of the warp totals finish it.  group(k) returns group k.
+constexpr int kKeGroup = 8;
+template <typename G>
+__device__ inline void ke_reduce(G group, int ng, DevScalars* sc, int damped)
 {
     __shared__ double s[kKeThreads / 32];
     double x = 0.0;
-    // loads issued 16 at a time, added in index order (part[t], part[t + B], ...)
-    for (int b0 = threadIdx.x; b0 < np; b0 += 16 * blockDim.x) {
-        double v[16];
+    for (int k0 = threadIdx.x; k0 < ng; k0 += 8 * blockDim.x) {
+        double g[8];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int b = b0 + u * blockDim.x;
-            v[u] = b < np ? part[b] : 0.0;
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u * blockDim.x;
+            g[u] = k < ng ? group(k) : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-            if (b0 + u * (int)blockDim.x < np) x += v[u];
+        for (int u = 0; u < 8; ++u)
+            if (k0 + u * (int)blockDim.x < ng) x += g[u];
     }
     x = warp_sum(x);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -403,6 +407,75 @@ __device__ inline void ke_finalize(const double* __restrict__ part, int np, DevS
             sc->done = 1;
         }
     }
+}
+
+// from the np slice partials (groups summed here)
+__device__ inline void ke_finalize(const double* __restrict__ part, int np, DevScalars* sc, int damped)
+{
+    ke_reduce(
+        [&](int k) {
+            double v[kKeGroup];
+#pragma unroll
+            for (int u = 0; u < kKeGroup; ++u) v[u] = k * kKeGroup + u < np ? __ldcg(part + k * kKeGroup + u) : 0.0;
+            double g = 0.0;
+#pragma unroll
+            for (int u = 0; u < kKeGroup; ++u)
+                if (k * kKeGroup + u < np) g += v[u];
+            return g;
+        },
+        (np + kKeGroup - 1) / kKeGroup, sc, damped);
+}
+
+// from group sums already formed (through L2: other blocks wrote them)
+__device__ inline void ke_finalize_groups(const double* __restrict__ gpart, int ng, DevScalars* sc,
+                                          int damped)
+{
+    ke_reduce([&](int k) { return __ldcg(gpart + k); }, ng, sc, damped);
+}
+
+// A block of kThreads = kKeGroup warps (the slices kKeGroup b ... of block
+// b): its group sum, the warp sums (slice partials) added in slice order.
+__device__ inline void group_partial_store(double x, double* gpart, int n)
+{
+    __shared__ double s[kKeGroup];
+    x = warp_sum(x);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int np = (n + 31) >> 5;
+        double g = 0.0;
+        for (int u = 0; u < kKeGroup; ++u)
+            if ((int)blockIdx.x * kKeGroup + u < np) g += s[u];
+        gpart[blockIdx.x] = g;
+    }
+}
+
+// The sliced-ELL force pass and the finish pass (blocks of kThreads =
+// kKeGroup warps, so block b holds group b): each block stores its group
+// sum; the block that finishes last reduces the group sums with the same
+// threads and order as ke_finalize, so the KE has the same bits as in a
+// batch, without a launch of its own and with a kKeGroup-th of the FP64
+// additions left for one SM.  Every block has written its group sum
+// (ordered by the block barrier and the fence) before it takes its ticket.
+template <typename T>
+__device__ inline void ke_last_block(const StepArgs<T>& a, double ke, int damped)
+{
+    static_assert(kThreads == kKeThreads && kThreads == 32 * kKeGroup,
+                  "a block is one KE group and reduces with the KE kernel's threads");
+    const int np = (a.n + 31) >> 5;
+    double* gpart = a.ke_part + np;  // group sums after the slice partials
+    group_partial_store(ke, gpart, a.n);
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&a.sc->ke_ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    ke_finalize_groups(gpart, (np + kKeGroup - 1) / kKeGroup, a.sc, damped);
+    if (threadIdx.x == 0) a.sc->ke_ticket = 0;
 }
 
 // u <- u + d, FP64, or FP32 hi + packed lo (two-sum with renormalisation,
@@ -541,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass_b(StepArgs<T> a, int final
     if (a.dflag) final_step = *a.dflag == 0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double ke = i < a.n ? pass_b_particle<T, D>(a, i, final_step) : 0.0;
-    if (final_step) slice_partial_store(ke, a.ke_part, i, a.n);
+    if (final_step) ke_last_block(a, ke, 0);
 }
 
 // after S_d: constraints, u^{n+3/2} = u^{n+1/2} + dt v^{n+1}, KE contribution
@@ -572,15 +645,17 @@ __global__ void __launch_bounds__(kThreads) k_finish(StepArgs<T> a)
     if (a.sc->done || (a.dflag && *a.dflag == 0)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double ke = i < a.n ? finish_particle<T>(a, i) : 0.0;
-    slice_partial_store(ke, a.ke_part, i, a.n);
+    ke_last_block(a, ke, 1);
 }
 
-// one block: KE of the body, KE_max, step counters, relax test
+// one block: KE of the body, KE_max, step counters, relax test, after the
+// brick-tiled force pass of an undamped step (the sliced-ELL force pass and
+// the finish pass reduce the KE in their last block instead)
 __global__ void __launch_bounds__(kKeThreads) k_ke_final(const double* __restrict__ part, int np,
-                                                        DevScalars* sc, int damped, const int* dflag)
+                                                        DevScalars* sc, const int* dflag)
 {
-    if (sc->done) return;
-    ke_finalize(part, np, sc, dflag ? *dflag : damped);
+    if (sc->done || (dflag && *dflag)) return;  // a damped step: k_finish reduced it
+    ke_finalize(part, np, sc, 0);
 }
 
 // the random choice of the step (Eq. viscosity-reset) on the device, for

@@ -883,7 +883,8 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
         k_twist<T><<<nblocks(n), kThreads, 0, st>>>(n, b->r0, b->desc.twist[0], b->desc.twist[1],
                                                    b->desc.twist[2], b->desc.twist[3], bf);
     }
-    b->ke_blocks = b->nslices;  // one FP64 partial per 32-particle slice
+    // one FP64 partial per 32-particle slice, then one per group of 8 slices
+    b->ke_blocks = b->nslices + (b->nslices + 7) / 8;
     SRDR_TRY(dalloc(b, &b->ke_part, b->ke_blocks));
     SRDR_CK(cudaMemsetAsync(b->ke_part, 0, sizeof(double) * b->ke_blocks, st));
 

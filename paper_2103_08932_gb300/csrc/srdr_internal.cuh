@@ -63,6 +63,8 @@ struct DevScalars {
     int done;              // criterion met or error: later step kernels skip
     int status;            // 0, or a device error code (SRDR_ERR_*)
     long long err_index;   // first offending particle / cell for status
+    unsigned ke_ticket;    // blocks of the current KE-writing kernel that have finished (0 between kernels)
+    int pad_;
 };
 
 // FP32-mixed displacement record (float4): x, y, z hold hi = fl(u); w holds

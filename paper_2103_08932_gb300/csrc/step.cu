@@ -317,13 +317,16 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
             prof_end(b, SRDR_K_FINISH, ev);
             counted(SRDR_K_FINISH, 1);
         }
-        prof_begin(b, SRDR_K_KE, &ev);
-        const bool slices = tiled && (dev || !damp);
-        if (slices)
+        // the KE: reduced by the last block of the sliced-ELL force pass
+        // (undamped step) or of the finish pass (damped step); after the
+        // brick-tiled force pass, by two kernels of its own
+        if (tiled && (dev || !damp)) {
+            prof_begin(b, SRDR_K_KE, &ev);
             k_ke_slices<<<nb, kThreads, 0, q>>>(b->ke_pp, (int)b->n, b->ke_part, b->sc, A.dflag);
-        k_ke_final<<<1, kKeThreads, 0, q>>>(b->ke_part, b->nslices, b->sc, damp ? 1 : 0, A.dflag);
-        prof_end(b, SRDR_K_KE, ev);
-        counted(SRDR_K_KE, slices ? 2 : 1);
+            k_ke_final<<<1, kKeThreads, 0, q>>>(b->ke_part, b->nslices, b->sc, A.dflag);
+            prof_end(b, SRDR_K_KE, ev);
+            counted(SRDR_K_KE, 2);
+        }
         return SRDR_OK;
     };
 
