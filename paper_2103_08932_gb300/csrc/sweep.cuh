@@ -5,8 +5,11 @@
 // particles in the canonical order (colour, cell, particle id) with dt/2,
 // then in the exact reverse order with dt/2 (Sec. 3.1; pairwise variant
 // Sec. 3.2).  Cells of one colour have disjoint 3^d footprints (Sec. 3.4), so
-// they run concurrently and commute; the colours run one after another with
-// a bounded grid barrier in one cooperative launch.
+// they run concurrently and commute.  All colour phases run in one
+// cooperative launch, ordered either by a bounded grid barrier between
+// consecutive phases (k_sweep_all) or by each cell waiting only for the
+// cells whose footprints overlap its own (k_sweep_flow); both give the same
+// bits.
 //
 // Mapping: a warp holds G cells, one group of L = 32/G lanes per cell.  A
 // group stages in shared memory its cell's CSR rows, weights and per-particle
