@@ -38,7 +38,8 @@
  *       the cantilever.  Read it as the rotation about the cantilever axis
  *       (y_c, z_c): g = gamma (0, -(z - z_c), y - y_c), gamma = gamma0
  *       sin(pi x / (2L)), x from the clamped face; gamma0 = 20 g / H with the
- *       thickness H for "h" (as in the survey's reading of h / dp).  It is
+ *       thickness H for "h" (the paper's "h" there is a length of the body, not
+ *       the smoothing length).  It is
  *       added to gravity on every particle; dt's |a|max is the largest
  *       |g + end load + g_t| over the particles.
  *   R16 Explicit-viscosity comparator (ORA_DAMP_EXPLICIT, Sec. 3): the term of
