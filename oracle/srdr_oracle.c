@@ -33,20 +33,26 @@
  *   R12 dt fixed per body: Eq. time-step-criterion with |v|max = 0 and
  *       |a|max = the largest body-force magnitude, min'd with the implicit
  *       viscous limit 50 h^2 / (nu~ D), nu~ = eta / (alpha rho0).
+ *   R13 Neighbour order within a row: ascending particle id (the pairwise
+ *       scheme's pair updates, Sec. 3.2, depend on it; in the particle
+ *       scheme it only orders the roundings of the sums).
+ *   R14 Cell index ix = floor((x - x0)/r_c) in FP64, x0 = min_i x_i, clamped
+ *       to [0, n_x - 1] with n_x = floor((max - min)/r_c) + 1.
+ *   R15 Convergence (the paper runs to a fixed time): a relaxation stops after
+ *       the first step with KE < tol KE_max, KE_max the largest KE so far.
+ *   R16 Explicit-viscosity comparator (ORA_DAMP_EXPLICIT, Sec. 3): the term of
+ *       Eq. damping-term with eta itself (no random choice) is evaluated at
+ *       v^n and added to the acceleration of S_m; dt is min'd with the
+ *       explicit limit 0.5 h^2 / (nu D), nu = eta / rho0 (Eq.
+ *       viscous-criteria-o).
  *   R17 Twisting body force (Sec. 4.2): the printed g = (0, y gamma, z gamma)
  *       is radial, at odds with the "rotational body-force" that "twists"
  *       the cantilever.  Read it as the rotation about the cantilever axis
  *       (y_c, z_c): g = gamma (0, -(z - z_c), y - y_c), gamma = gamma0
  *       sin(pi x / (2L)), x from the clamped face; gamma0 = 20 g / H with the
  *       thickness H for "h" (the paper's "h" there is a length of the body, not
- *       the smoothing length).  It is
- *       added to gravity on every particle; dt's |a|max is the largest
- *       |g + end load + g_t| over the particles.
- *   R16 Explicit-viscosity comparator (ORA_DAMP_EXPLICIT, Sec. 3): the term of
- *       Eq. damping-term with eta itself (no random choice) is evaluated at
- *       v^n and added to the acceleration of S_m; dt is min'd with the
- *       explicit limit 0.5 h^2 / (nu D), nu = eta / rho0 (Eq.
- *       viscous-criteria-o).
+ *       the smoothing length).  It is added to gravity on every particle;
+ *       dt's |a|max is the largest |g + end load + g_t| over the particles.
  */
 #include "srdr_oracle.h"
 
