@@ -55,3 +55,17 @@ def test_invalid_description_is_rejected_without_gpu(L):
         srdr.srdr_body_create(d)
     assert e.value.status == srdr.SRDR_ERR_INVALID
     assert "dim" in srdr.last_error()
+
+
+def test_body_controls_reject_a_null_body_without_gpu(L):
+    """The mapping and synchronisation controls and the failure-path hook
+    check their arguments on the host before any device call."""
+    calls = [
+        lambda: L.srdr_body_sweep_sync(None, srdr.SRDR_SWEEP_CELLS),
+        lambda: L.srdr_body_debug_stall_sweep(None),
+        lambda: L.srdr_body_tune(None, 1, 1),
+        lambda: L.srdr_body_pass_mapping(None, srdr.SRDR_PASS_SELL, 0, 0, 0),
+    ]
+    for call in calls:
+        assert call() == srdr.SRDR_ERR_INVALID
+        assert srdr.last_error()
