@@ -248,8 +248,9 @@ struct CellStage {
 };
 
 // Stage the read-only data of cell c: footprint runs, row starts, CSR weights
-// and footprint-local indices, masses and weight sums.  The copies are
-// asynchronous; run_cell waits for them.
+// and footprint-local indices (16-byte chunks), masses and the local solve's
+// constants, and the footprint index table (plain shared-memory stores).  The
+// copies are asynchronous; run_cell waits for them.
 template <typename T, int D, int L>
 __device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellSmem<T, D>& s, int gl,
                                        unsigned gmask)
@@ -294,11 +295,11 @@ __device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellS
     return st;
 }
 
-// Sweep the staged cell: fetch the footprint's velocity records, then the
-// local operators of its particles in order (mode 0), in reverse order
-// (mode 1) or in order and then in reverse order (mode 2: the last colour's
-// forward and backward phases, fused since its cells' footprints are
-// disjoint), then write the footprint back.
+// Sweep the staged cell: copy the footprint's velocity records from L2 into
+// shared memory, then apply the local operators of its particles in order
+// (mode 0), in reverse order (mode 1) or in order and then in reverse order
+// (mode 2: the last colour's forward and backward phases, fused since its
+// cells' footprints are disjoint), then write the footprint back through L2.
 template <typename T, int D, int L>
 __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int mode,
                                 const CellSmem<T, D>& s, int gl, unsigned gmask)
@@ -540,7 +541,8 @@ __device__ inline int next_item(const int* __restrict__ colour_ptr, int ncolours
 
 // The whole S_d of one damped step in one cooperative launch: colours
 // 0..3^d-1 forward, then 3^d-1..0 backward, a bounded grid barrier between
-// colour phases; the last colour runs both directions in one phase.  Blocks of W warps, G cell groups per warp; group number
+// colour phases; the last colour runs both directions in one phase.  Blocks
+// of W warps, G cell groups per warp; group number
 // q = (block * W + warp) * G + g takes the colour's cells q, q + gridDim*W*G, ...
 // More warps per block means fewer blocks arriving at the grid barrier.
 template <typename T, int D, int G, int W>
@@ -606,9 +608,9 @@ __global__ void __launch_bounds__(32 * W) k_sweep_all(SweepArgs<T> a, const int*
 // The same S_d without grid barriers.  The canonical order only constrains
 // cells whose footprints overlap, i.e. cells within 2 cells of each other on
 // every axis (5^d - 1 of them; same-colour cells are 3 apart, so none of them
-// shares a colour with the cell).  Each cell counts the phases it has
-// finished; before its phase ph a cell waits until every non-empty cell of
-// its 5^d neighbourhood has finished all of its own phases that precede ph,
+// shares a colour with the cell).  Each cell counts the sweep directions it
+// has finished; before its phase ph a cell waits until every non-empty cell
+// of its 5^d neighbourhood has finished all of its own phases that precede ph,
 // and its later phases wait in turn for this one.  Every pair of overlapping
 // cells is therefore ordered as in the canonical order, so the result is
 // bitwise that of k_sweep_all; regions of the body that are ready run ahead
