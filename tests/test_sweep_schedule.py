@@ -45,10 +45,12 @@ def overlapping(a, b):
     return a != b and all(abs(a[k] - b[k]) <= 2 for k in range(3))
 
 
-def simulate(shape, dim, occupied, ngroups, sweeps, seed):
+def simulate(shape, dim, occupied, ngroups, sweeps, seed, fused=None):
     """Run `sweeps` sweeps under the cell-wise rule with a random interleaving
     of the groups; return the global execution order of (sweep, phase, cell)
-    or raise on a deadlock."""
+    or raise on a deadlock.  fused[s] is the colour whose two directions sweep
+    s fuses: the body's own last colour alone, the batch's last colour (which
+    may have no cell in this body) in a batch; default: the body's own."""
     rnd = random.Random(seed)
     nc = 27 if dim == 3 else 9
     cells_by_colour = [[] for _ in range(nc)]
@@ -56,17 +58,18 @@ def simulate(shape, dim, occupied, ngroups, sweeps, seed):
         cells_by_colour[colour(c, dim)].append(c)
     for lst in cells_by_colour:
         rnd.shuffle(lst)  # the kernel's colour lists have no set order
-    clast = max(k for k in range(nc) if cells_by_colour[k])
-    phases = []
-    for ph in range(2 * nc):
-        col = ph if ph < nc else 2 * nc - 1 - ph
-        if not cells_by_colour[col] or (ph >= nc and col == clast):
-            continue
-        phases.append((ph, col))
+    own_last = max(k for k in range(nc) if cells_by_colour[k])
     done = {c: 0 for c in occupied}
     epoch = 0
     order = []
     for s in range(sweeps):
+        clast = fused[s] if fused else own_last
+        phases = []
+        for ph in range(2 * nc):
+            col = ph if ph < nc else 2 * nc - 1 - ph
+            if not cells_by_colour[col] or (ph >= nc and col == clast):
+                continue
+            phases.append((ph, col))
         # group q takes items q, q + ngroups, ... of each phase, in phase order
         queues = [[] for _ in range(ngroups)]
         for ph, col in phases:
@@ -122,3 +125,26 @@ def test_overlapping_cells_never_share_a_colour():
             for b in neighbourhood(a, (6, 6, 6 if dim == 3 else 1), dim):
                 assert colour(a, dim) != colour(b, dim)
 
+
+
+@pytest.mark.parametrize("dim,shape,fill,seed", [(2, (8, 2, 1), 0.9, 7), (3, (5, 5, 2), 0.8, 8),
+                                                 (3, (4, 2, 3), 1.0, 9)])
+def test_counts_stay_consistent_between_single_and_batched_sweeps(dim, shape, fill, seed):
+    """A body alternates between single-body sweeps (its own last colour
+    fused) and batched sweeps (the batch's last colour fused, possibly a
+    colour the body has no cell of, so the body's own last colour runs its two
+    directions apart).  Counting two directions per sweep keeps every wait
+    satisfiable and the canonical order of each sweep."""
+    rnd = random.Random(200 + seed)
+    cells = [c for c in itertools.product(range(shape[0]), range(shape[1]), range(shape[2]))]
+    occupied = {c for c in cells if rnd.random() < fill} or {cells[0]}
+    nc = 27 if dim == 3 else 9
+    own = max(colour(c, dim) for c in occupied)
+    assert own < nc - 1  # the batch fuses a colour this body has no cell of
+    fused = [own, nc - 1, own, nc - 1, nc - 1, own]
+    order = simulate(shape, dim, occupied, 3, sweeps=len(fused), seed=seed, fused=fused)
+    pos = {item: k for k, item in enumerate(order)}
+    for (s, ph, a), ka in pos.items():
+        for (t, qh, b), kb in pos.items():
+            if overlapping(a, b) and (s, ph) < (t, qh):
+                assert ka < kb, ((s, ph, a), (t, qh, b))
