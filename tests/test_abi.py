@@ -57,15 +57,26 @@ def test_invalid_description_is_rejected_without_gpu(L):
     assert "dim" in srdr.last_error()
 
 
-def test_body_controls_reject_a_null_body_without_gpu(L):
-    """The mapping and synchronisation controls and the failure-path hook
-    check their arguments on the host before any device call."""
+def test_entry_points_reject_null_handles_without_gpu(L):
+    """Body, batch and control entry points (and the failure-path hook) check
+    their handles on the host before any device call."""
     calls = [
         lambda: L.srdr_body_sweep_sync(None, srdr.SRDR_SWEEP_CELLS),
         lambda: L.srdr_body_debug_stall_sweep(None),
         lambda: L.srdr_body_tune(None, 1, 1),
         lambda: L.srdr_body_pass_mapping(None, srdr.SRDR_PASS_SELL, 0, 0, 0),
+        lambda: L.srdr_body_step(None, 1),
+        lambda: L.srdr_body_relax(None, 1e-8, 10, None, None),
+        lambda: L.srdr_body_read_displacement(None, None, 0),
+        lambda: L.srdr_body_read_velocity(None, None, 0),
+        lambda: L.srdr_body_write_state(None, None, None, 0, 0.0),
+        lambda: L.srdr_body_stats(None, None),
+        lambda: L.srdr_batch_step(None, 1),
+        lambda: L.srdr_batch_info(None, None, None, None, None),
     ]
     for call in calls:
         assert call() == srdr.SRDR_ERR_INVALID
         assert srdr.last_error()
+    # destroying a null handle is a no-op
+    L.srdr_body_destroy(None)
+    L.srdr_batch_destroy(None)
