@@ -21,6 +21,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "srdr_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libsrdr_oracle.so")
+# the same source built with OpenMP (stress / force loops over particles, the
+# cells of one colour of the damping sweep over threads): identical bits
+_LIB_OMP = os.path.join(_HERE, "_build", "libsrdr_oracle_omp.so")
 
 SVK, NEO_HOOKEAN = 0, 1
 DAMP_NONE, DAMP_PARTICLE, DAMP_PAIRWISE, DAMP_EXPLICIT = 0, 1, 2, 3
@@ -29,18 +32,24 @@ FLAG_CONSTRAINED, FLAG_END_LOAD = 1, 2
 U, V, F, PB, B0, ACC = 0, 1, 2, 3, 4, 5
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction) if it is out of date."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(os.path.join(_HERE, "srdr_oracle.h"))):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+def _build_one(out: str, extra, force: bool) -> str:
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(out) >= os.path.getmtime(os.path.join(_HERE, "srdr_oracle.h"))):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+                           *extra, "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction) if it is out of date:
+    the serial library and the OpenMP one."""
+    _build_one(_LIB_OMP, ["-fopenmp"], force)
+    return _build_one(_LIB, [], force)
 
 
 class _Params(C.Structure):
@@ -58,13 +67,29 @@ class _Params(C.Structure):
 
 
 _lib = None
+_lib_omp = None
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The serial oracle library, or with omp=True its OpenMP build."""
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(C.CDLL(_LIB_OMP))
+        return _lib_omp
     if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
+        _lib = _declare(C.CDLL(build()))
+    return _lib
+
+
+def threads_available() -> int:
+    """Threads the OpenMP build uses by default (the host's cores)."""
+    return int(lib(True).ora_threads())
+
+
+def _declare(L):
+    if True:
         d, i64, p = C.c_double, C.c_int64, C.c_void_p
         L.ora_kernel_W.restype = d
         L.ora_kernel_W.argtypes = [C.c_int, d, d]
@@ -105,7 +130,9 @@ def lib():
         L.ora_body_viscous_acc.argtypes = [p, d, p, p]
         L.ora_twist_force.argtypes = [p, p, p]
         L.ora_body_local_update.argtypes = [p, i64, d, d, p]
-    return _lib
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_threads.restype = C.c_int
+    return L
 
 
 def _ptr(a: np.ndarray):
@@ -228,7 +255,13 @@ class Params:
 class OracleBody:
     """An oracle body over arbitrary reference positions r0 (n, dim)."""
 
-    def __init__(self, params: Params, r0, vol=None, vol_default=None, flags=None, u0=None):
+    def __init__(self, params: Params, r0, vol=None, vol_default=None, flags=None, u0=None,
+                 threads: int = 0):
+        """threads > 0: step on the OpenMP build with that many threads (the
+        same bits as the serial build); 0: the serial build."""
+        self._L = lib(True) if threads > 0 else lib()
+        if threads > 0:
+            self._L.ora_set_threads(int(threads))
         self.params = params
         dim = params.dim
         self.dim = dim
@@ -253,57 +286,57 @@ class OracleBody:
         err = C.create_string_buffer(256)
         self._cp = params.to_c()
         vd = float(vol_default) if vol_default is not None else 0.0
-        self._h = lib().ora_body_create(C.byref(self._cp), self.n, _ptr(r), vp, vd, fp, up, err, 256)
+        self._h = self._L.ora_body_create(C.byref(self._cp), self.n, _ptr(r), vp, vd, fp, up, err, 256)
         if not self._h:
             raise ValueError("oracle body: " + err.value.decode())
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().ora_body_destroy(h)
+            self._L.ora_body_destroy(h)
             self._h = None
 
     # scalars
     @property
     def nnz(self):
-        return lib().ora_body_nnz(self._h)
+        return self._L.ora_body_nnz(self._h)
 
     @property
     def dt(self):
-        return lib().ora_body_dt(self._h)
+        return self._L.ora_body_dt(self._h)
 
     @property
     def eta(self):
-        return lib().ora_body_eta(self._h)
+        return self._L.ora_body_eta(self._h)
 
     @property
     def step_index(self):
-        return lib().ora_body_step_index(self._h)
+        return self._L.ora_body_step_index(self._h)
 
     @property
     def ke(self):
-        return lib().ora_body_ke(self._h)
+        return self._L.ora_body_ke(self._h)
 
     @property
     def ke_max(self):
-        return lib().ora_body_ke_max(self._h)
+        return self._L.ora_body_ke_max(self._h)
 
     @property
     def damped_steps(self):
-        return lib().ora_body_damped_steps(self._h)
+        return self._L.ora_body_damped_steps(self._h)
 
     # arrays
     def get(self, what):
         w = 3 if what in (U, V, ACC) else 9
         out = np.zeros((self.n, w))
-        lib().ora_body_get(self._h, what, _ptr(out))
+        self._L.ora_body_get(self._h, what, _ptr(out))
         return out if w == 3 else out.reshape(self.n, 3, 3)
 
     def set(self, what, arr):
         a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(self.n, -1))
         if what in (U, V) and a.shape[1] != 3:
             a = _vec3(a, self.dim)
-        lib().ora_body_set(self._h, what, _ptr(a))
+        self._L.ora_body_set(self._h, what, _ptr(a))
 
     @property
     def u(self):
@@ -316,53 +349,53 @@ class OracleBody:
     def neighbours(self):
         row = np.zeros(self.n + 1, dtype=np.int64)
         col = np.zeros(max(self.nnz, 1), dtype=np.int64)
-        lib().ora_body_neighbours(self._h, _ptr(row), _ptr(col))
+        self._L.ora_body_neighbours(self._h, _ptr(row), _ptr(col))
         return row, col[: self.nnz]
 
     def cells(self):
         cell = np.zeros(self.n, dtype=np.int64)
         colour = np.zeros(self.n, dtype=np.int32)
         order = np.zeros(self.n, dtype=np.int64)
-        lib().ora_body_cells(self._h, _ptr(cell), _ptr(colour), _ptr(order))
+        self._L.ora_body_cells(self._h, _ptr(cell), _ptr(colour), _ptr(order))
         return cell, colour, order
 
     def step(self, nsteps=1):
-        return lib().ora_body_step(self._h, nsteps)
+        return self._L.ora_body_step(self._h, nsteps)
 
     def relax(self, tol=1e-8, max_steps=10**7):
         st, ratio = C.c_int64(), C.c_double()
-        status = lib().ora_body_relax(self._h, tol, max_steps, C.byref(st), C.byref(ratio))
+        status = self._L.ora_body_relax(self._h, tol, max_steps, C.byref(st), C.byref(ratio))
         return status, st.value, ratio.value
 
     def F_from_u(self, u):
         ua = _vec3(u, self.dim)
         out = np.zeros((self.n, 9))
-        lib().ora_body_F_from_u(self._h, _ptr(ua), _ptr(out))
+        self._L.ora_body_F_from_u(self._h, _ptr(ua), _ptr(out))
         return out.reshape(self.n, 3, 3)
 
     def Fdot(self, v):
         va = _vec3(v, self.dim)
         out = np.zeros((self.n, 9))
-        lib().ora_body_Fdot(self._h, _ptr(va), _ptr(out))
+        self._L.ora_body_Fdot(self._h, _ptr(va), _ptr(out))
         return out.reshape(self.n, 3, 3)
 
     def acc(self, F):
         Fa = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(self.n, 9))
         out = np.zeros((self.n, 3))
-        lib().ora_body_acc(self._h, _ptr(Fa), _ptr(out))
+        self._L.ora_body_acc(self._h, _ptr(Fa), _ptr(out))
         return out
 
     def viscous_acc(self, eta, v):
         """Eq. damping-term for the velocity field v (explicit comparator)."""
         va = _vec3(v, self.dim)
         out = np.zeros((self.n, 3))
-        lib().ora_body_viscous_acc(self._h, eta, _ptr(va), _ptr(out))
+        self._L.ora_body_viscous_acc(self._h, eta, _ptr(va), _ptr(out))
         return out
 
     def damp(self, eta_tilde, dt_loc):
-        lib().ora_body_damp(self._h, eta_tilde, dt_loc)
+        self._L.ora_body_damp(self._h, eta_tilde, dt_loc)
 
     def local_update(self, i, eta_tilde, dt_loc, v):
         va = _vec3(v, self.dim).copy()
-        lib().ora_body_local_update(self._h, int(i), eta_tilde, dt_loc, _ptr(va))
+        self._L.ora_body_local_update(self._h, int(i), eta_tilde, dt_loc, _ptr(va))
         return va

@@ -60,6 +60,33 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads.  The same source builds serially and, with -fopenmp, with the
+ * per-particle loops of the stress and force evaluation and the cells of one
+ * colour of the damping sweep spread over threads.  Neither changes a
+ * rounding: every particle's sums run in the same order on one thread, the
+ * cells of one colour touch disjoint particles (Sec. 3.4), and the kinetic
+ * energy is summed serially.  The two builds give identical bits. */
+void ora_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int ora_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define ORA_PI 3.14159265358979323846
 
@@ -403,6 +430,11 @@ struct ora_body {
     int* colour;
     int64_t* order; /* canonical sweep order */
     int64_t ncell[3];
+    /* the cells of the sweep as runs of the canonical order: run r covers
+     * order[run[r] .. run[r+1]-1]; colour c owns runs colour_run[c] ..
+     * colour_run[c+1]-1 */
+    int64_t nrun;
+    int64_t *run, *colour_run;
     /* state */
     double *u, *v, *F, *PB, *acc;
     int64_t step;
@@ -416,6 +448,7 @@ static void body_free(ora_body* b)
     free(b->r0); free(b->vol); free(b->mass); free(b->flags);
     free(b->row_ptr); free(b->col); free(b->dW); free(b->rij); free(b->e);
     free(b->B0); free(b->cell); free(b->colour); free(b->order);
+    free(b->run); free(b->colour_run);
     free(b->u); free(b->v); free(b->F); free(b->PB); free(b->acc);
     free(b);
 }
@@ -612,6 +645,23 @@ ora_body* ora_body_create(const ora_params* p, int64_t n, const double* r0, cons
     b->colour = (int*)malloc(sizeof(int) * (size_t)n);
     b->order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
     ora_cells(p->dim, n, b->r0, 2.0 * p->h, b->cell, b->colour, b->ncell, b->order);
+    {
+        int ncol = p->dim == 2 ? 9 : 27;
+        b->run = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+        b->colour_run = (int64_t*)calloc((size_t)ncol + 1, sizeof(int64_t));
+        int64_t r = 0;
+        for (int64_t s = 0; s < n; ++s) {
+            int64_t i = b->order[s];
+            if (s == 0 || b->cell[i] != b->cell[b->order[s - 1]]) {
+                b->run[r++] = s;
+                b->colour_run[b->colour[i] + 1] = r;
+            }
+        }
+        b->run[r] = n;
+        b->nrun = r;
+        for (int c = 1; c <= ncol; ++c)
+            if (b->colour_run[c] < b->colour_run[c - 1]) b->colour_run[c] = b->colour_run[c - 1];
+    }
 
     /* fixed reference neighbours and reference kernel gradients */
     build_neighbours_cll(b);
@@ -702,6 +752,7 @@ void ora_body_cells(const ora_body* b, int64_t* cell, int* colour, int64_t* orde
 void ora_body_F_from_u(const ora_body* b, const double* u, double* F_out)
 {
     int dim = b->p.dim;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < b->n; ++i) {
         double G[9], GB[9];
         mat_zero(G);
@@ -725,6 +776,7 @@ void ora_body_F_from_u(const ora_body* b, const double* u, double* F_out)
 void ora_body_Fdot(const ora_body* b, const double* v, double* Fdot_out)
 {
     int dim = b->p.dim;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < b->n; ++i) {
         double G[9], GB[9];
         mat_zero(G);
@@ -748,12 +800,14 @@ void ora_body_acc(const ora_body* b, const double* F, double* acc_out)
 {
     int dim = b->p.dim;
     ora_body* bm = (ora_body*)b;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < b->n; ++i) {
         double S[9], P[9];
         ora_pk2(dim, b->p.material, b->lambda, b->mu, F + i * 9, S);
         mat_mul(dim, F + i * 9, S, P);
         mat_mul(dim, P, b->B0 + i * 9, bm->PB + i * 9);
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < b->n; ++i) {
         double a[3] = {0, 0, 0};
         for (int64_t k = b->row_ptr[i]; k < b->row_ptr[i + 1]; ++k) {
@@ -800,6 +854,7 @@ void ora_twist_force(const ora_params* p, const double r[3], double out[3])
 void ora_body_viscous_acc(const ora_body* b, double eta, const double* v, double* out)
 {
     int dim = b->p.dim;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < b->n; ++i) {
         double a[3] = {0, 0, 0};
         double Vi = b->mass[i] / b->p.rho0;
@@ -886,10 +941,22 @@ void ora_body_local_update(const ora_body* b, int64_t i, double eta_tilde, doubl
  * is already the half step. */
 void ora_body_damp(ora_body* b, double eta_tilde, double dt_loc)
 {
-    for (int64_t s = 0; s < b->n; ++s)
-        ora_body_local_update(b, b->order[s], eta_tilde, dt_loc, b->v);
-    for (int64_t s = b->n - 1; s >= 0; --s)
-        ora_body_local_update(b, b->order[s], eta_tilde, dt_loc, b->v);
+    /* The canonical order, taken colour by colour: the runs (cells) of one
+     * colour touch disjoint particles, so they may run in any order or at the
+     * same time and give the serial result. */
+    int ncol = b->p.dim == 2 ? 9 : 27;
+    for (int c = 0; c < ncol; ++c) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t r = b->colour_run[c]; r < b->colour_run[c + 1]; ++r)
+            for (int64_t s = b->run[r]; s < b->run[r + 1]; ++s)
+                ora_body_local_update(b, b->order[s], eta_tilde, dt_loc, b->v);
+    }
+    for (int c = ncol - 1; c >= 0; --c) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t r = b->colour_run[c + 1] - 1; r >= b->colour_run[c]; --r)
+            for (int64_t s = b->run[r + 1] - 1; s >= b->run[r]; --s)
+                ora_body_local_update(b, b->order[s], eta_tilde, dt_loc, b->v);
+    }
 }
 
 static void impose_constraints(ora_body* b)

@@ -55,6 +55,10 @@ typedef struct {
     double twist[4];
 } ora_params;
 
+/* threads of the OpenMP build (ignored by the serial build); identical bits */
+void ora_set_threads(int nthreads);
+int  ora_threads(void);
+
 /* ---- closed pieces ---------------------------------------------------- */
 double ora_kernel_W(int dim, double h, double r);    /* Wendland C2 */
 double ora_kernel_dW(int dim, double h, double r);   /* dW/dr */
