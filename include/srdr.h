@@ -313,12 +313,16 @@ void srdr_batch_destroy(srdr_batch* batch);
  * (srdr_body_relax).  Internally synchronised. */
 typedef struct srdr_server srdr_server;
 typedef struct {
-    int64_t submitted, completed, refused, queued, in_flight;
+    int64_t submitted;
+    int64_t completed;            /* solves: requests that met their KE criterion (SRDR_OK) */
+    int64_t refused, queued, in_flight;
     int peak_concurrent;          /* most bodies live at once */
     size_t bytes_in_use;          /* admitted device-memory estimate */
     int64_t particle_steps;       /* over all finished chunks */
-    double p50_latency_s, p99_latency_s;  /* submit -> result, completed requests */
-    double solves_per_s;          /* completed / (last completion - first submit) */
+    double p50_latency_s, p99_latency_s;  /* submit -> result, solves only */
+    double solves_per_s;          /* completed / (last retirement of any request - first submit) */
+    int64_t not_converged;        /* retired at max_steps (SRDR_ERR_NOT_CONVERGED): not solves */
+    int64_t failed;               /* retired with another error (non-finite KE, build failure) */
 } srdr_server_report;
 
 /* device_mem_budget: bytes the live bodies may hold; cuda_stream as for bodies

@@ -89,6 +89,7 @@ struct srdr_server {
     // statistics
     std::vector<double> latencies;
     int64_t submitted = 0, completed = 0, refused = 0;
+    int64_t not_converged = 0, failed = 0;
     int peak_live = 0;
     double t_first_submit = 0, t_last_done = 0;
     int64_t particle_steps = 0;
@@ -115,9 +116,18 @@ void finish(srdr_server* s, Live& l, srdr_status st)
     std::lock_guard<std::mutex> lock(s->mu);
     s->in_use -= std::min(s->in_use, l.bytes);
     s->in_flight.erase(l.ticket);
+    // only a request that met its KE criterion counts as a solve (and in the
+    // latency percentiles); one retired at the step cap or by an error is
+    // counted apart
+    if (r.status == SRDR_OK) {
+        s->latencies.push_back(t - l.t_submit);
+        s->completed += 1;
+    } else if (r.status == SRDR_ERR_NOT_CONVERGED) {
+        s->not_converged += 1;
+    } else {
+        s->failed += 1;
+    }
     s->results[l.ticket] = std::move(r);
-    s->latencies.push_back(t - l.t_submit);
-    s->completed += 1;
     s->t_last_done = t;
     s->cv_done.notify_all();
 }
@@ -377,6 +387,8 @@ srdr_status srdr_server_stats(srdr_server* s, srdr_server_report* out)
     out->peak_concurrent = s->peak_live;
     out->bytes_in_use = s->in_use;
     out->particle_steps = s->particle_steps;
+    out->not_converged = s->not_converged;
+    out->failed = s->failed;
     std::vector<double> l = s->latencies;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
@@ -386,9 +398,9 @@ srdr_status srdr_server_stats(srdr_server* s, srdr_server_report* out)
         };
         out->p50_latency_s = pct(0.50);
         out->p99_latency_s = pct(0.99);
-        const double span = s->t_last_done - s->t_first_submit;
-        out->solves_per_s = span > 0 ? s->completed / span : 0.0;
     }
+    const double span = s->t_last_done - s->t_first_submit;
+    out->solves_per_s = span > 0 ? s->completed / span : 0.0;
     return SRDR_OK;
 }
 

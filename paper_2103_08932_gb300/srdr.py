@@ -397,7 +397,8 @@ class srdr_server_report(C.Structure):
                 ("queued", C.c_int64), ("in_flight", C.c_int64), ("peak_concurrent", C.c_int),
                 ("bytes_in_use", C.c_size_t), ("particle_steps", C.c_int64),
                 ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
-                ("solves_per_s", C.c_double)]
+                ("solves_per_s", C.c_double), ("not_converged", C.c_int64),
+                ("failed", C.c_int64)]
 
 
 def _server_sigs(L):

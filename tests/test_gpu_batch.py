@@ -113,3 +113,51 @@ def test_batch_step_cap_reports_not_converged():
     status, st, steps = batch.run(1e-12, 50)
     assert status == srdr.SRDR_ERR_NOT_CONVERGED
     assert list(st) == [srdr.SRDR_ERR_NOT_CONVERGED] and list(steps) == [50]
+
+
+def _oracle(spec):
+    from oracle import oracle as O
+    r0, flags, u0 = S.lattice(spec)
+    p = O.Params(dim=spec.dim, material=spec.material, rho0=spec.rho0, E=spec.E, nu=spec.nu,
+                 h=spec.h, gravity=spec.gravity, end_load=spec.end_load, beta=spec.beta,
+                 L_char=spec.L_char, alpha=spec.alpha, seed=spec.seed)
+    return O.OracleBody(p, r0[:, :spec.dim], vol_default=spec.vol, flags=flags)
+
+
+@pytest.mark.parametrize("precision", [srdr.SRDR_FP64, srdr.SRDR_FP32_MIXED])
+def test_batched_bodies_at_convergence_match_oracle(precision):
+    """Two uneven bodies relaxed together as one batch against the FP64 oracle
+    relaxing each of them alone (KE/KE_max < 1e-6): FP64 stops at the
+    oracle's step within rounding; FP32-mixed is compared at the oracle's
+    stopping step, within 1e-4 relative max displacement."""
+    specs = uneven_specs(3)[:2]
+    tol = 1e-6
+    want = []
+    for s in specs:
+        ob = _oracle(s)
+        st, steps, _ = ob.relax(tol, 200000)
+        assert st == 0
+        want.append((steps, ob.u, ob.damped_steps))
+    bodies = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
+    batch = srdr.Batch(bodies)
+    if precision == srdr.SRDR_FP64:
+        status, st, steps = batch.run(tol, 200000)
+        assert status == srdr.SRDR_OK
+        assert list(steps) == [w[0] for w in want]
+    else:
+        # step the batch to each oracle stopping step in turn
+        order = sorted(range(len(specs)), key=lambda k: want[k][0])
+        done = 0
+        got = [None] * len(specs)
+        for k in order:
+            batch.step(want[k][0] - done)
+            done = want[k][0]
+            got[k] = bodies[k].displacement()
+    for k, (b, (steps, u, damped)) in enumerate(zip(bodies, want)):
+        ug = b.displacement() if precision == srdr.SRDR_FP64 else got[k]
+        err = np.abs(ug - u).max() / np.abs(u).max()
+        assert err <= 1e-4
+        if precision == srdr.SRDR_FP64:
+            assert err <= 1e-9
+            assert b.stats()["damped_steps"] == damped
+    batch.close()

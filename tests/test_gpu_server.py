@@ -97,6 +97,52 @@ def test_server_isolates_faulty_requests():
         assert st == wst == srdr.SRDR_OK
         assert steps == wsteps
         assert np.array_equal(got, u)
+    rep = srv.stats()
+    # only the two converged requests are solves; the faulty ones are counted apart
+    assert rep["completed"] == 2 and rep["failed"] == 2 and rep["not_converged"] == 0
+    srv.close()
+
+
+def test_server_step_capped_request_is_not_a_solve():
+    """A request retired at max_steps before its KE criterion is reported as
+    SRDR_ERR_NOT_CONVERGED and counted apart: it adds nothing to the solves,
+    the solves per second or the latency percentiles."""
+    sp = specs()[0]
+    srv = srdr.Server(8 << 30, ke_ratio=TOL, max_steps=128, max_bodies=4, chunk_steps=64)
+    st, t = srv.submit(srdr.make_desc(sp))
+    assert st == srdr.SRDR_OK
+    st, _, _, steps = srv.wait(t, 600.0)
+    assert st == srdr.SRDR_ERR_NOT_CONVERGED and steps == 128
+    rep = srv.stats()
+    assert rep["completed"] == 0 and rep["not_converged"] == 1 and rep["failed"] == 0
+    assert rep["solves_per_s"] == 0.0
+    assert rep["p50_latency_s"] == 0.0 and rep["p99_latency_s"] == 0.0
+    srv.close()
+
+
+def test_served_results_match_oracle():
+    """Two requests served together (FP64) against the FP64 oracle relaxing
+    each body alone to the same criterion: the same stopping step and the
+    same displacement within rounding (and within the 1e-4 bar)."""
+    from oracle import oracle as O
+    sp = specs()[:2]
+    want = []
+    for s in sp:
+        r0, flags, _ = S.lattice(s)
+        p = O.Params(dim=3, material=s.material, rho0=s.rho0, E=s.E, nu=s.nu, h=s.h,
+                     gravity=s.gravity, beta=s.beta, L_char=s.L_char, alpha=s.alpha, seed=s.seed)
+        ob = O.OracleBody(p, r0, vol_default=s.vol, flags=flags)
+        st, steps, _ = ob.relax(TOL, 200000)
+        assert st == 0
+        want.append((steps, ob.u))
+    srv = srdr.Server(8 << 30, ke_ratio=TOL, max_steps=200000, max_bodies=4, chunk_steps=128)
+    tickets = [srv.submit(srdr.make_desc(s))[1] for s in sp]
+    for t, (steps, u) in zip(tickets, want):
+        st, got, _, nsteps = srv.wait(t, 600.0)
+        assert st == srdr.SRDR_OK and nsteps == steps
+        err = np.abs(got - u).max() / np.abs(u).max()
+        assert err <= 1e-4
+        assert err <= 1e-9  # FP64 against FP64
     srv.close()
 
 
