@@ -25,7 +25,7 @@ def _built():
     srdr.lib()
 
 
-def oracle_for(spec, **kw):
+def oracle_for(spec, threads=0, **kw):
     r0, flags, u0 = S.lattice(spec)
     p = O.Params(dim=spec.dim, material=spec.material, rho0=spec.rho0, E=spec.E, nu=spec.nu,
                  h=spec.h, gravity=spec.gravity, end_load=spec.end_load, beta=spec.beta,
@@ -34,7 +34,7 @@ def oracle_for(spec, **kw):
         setattr(p, k, v)
     has_u0 = np.abs(u0).max() > 0
     return O.OracleBody(p, r0[:, :spec.dim], vol_default=spec.vol, flags=flags,
-                        u0=u0[:, :spec.dim] if has_u0 else None)
+                        u0=u0[:, :spec.dim] if has_u0 else None, threads=threads)
 
 
 def rel(a, b):
@@ -64,6 +64,51 @@ def test_cantilever_2d_fp32_mixed_at_oracle_step():
     gb = srdr.Body(srdr.make_desc(spec, precision=srdr.SRDR_FP32_MIXED))
     gb.step(steps_o)
     assert rel(gb.displacement(), ob.u) <= 1e-4
+
+
+_ORACLE_RELAXED = {}
+
+
+def oracle_relaxed(name, spec, **kw):
+    """The oracle relaxed to KE/KE_max < 1e-8 (OpenMP build on every host
+    core: the same bits as the serial build), cached per body."""
+    if name not in _ORACLE_RELAXED:
+        import os
+        ob = oracle_for(spec, threads=os.cpu_count() or 1, **kw)
+        st, steps, _ = ob.relax(1e-8, 400000)
+        assert st == 0
+        _ORACLE_RELAXED[name] = (steps, ob.u, ob.damped_steps)
+    return _ORACLE_RELAXED[name]
+
+
+RELAX3D = [("plate-x0.3", S.scaled(S.cantilever_plate_3d(), 0.3), {}),
+           ("block-16mm", S.compression_block_3d(dp=1e-3, edge=0.016), {"f_form": O.F_DISPLACEMENT})]
+
+
+@pytest.mark.parametrize("name,spec,kw", RELAX3D, ids=[c[0] for c in RELAX3D])
+@pytest.mark.parametrize("precision", [srdr.SRDR_FP64, srdr.SRDR_FP32_MIXED])
+def test_3d_relaxed_against_oracle(name, spec, kw, precision):
+    """3D bodies relaxed to KE/KE_max < 1e-8: the plate scaled x0.3 (60 x 6 x
+    30 + 3 clamped layers, 11,340 particles) and the compression block (16 mm
+    cube at dp = 1 mm, 5,632 particles).  The GPU run converges; FP64 stops
+    at the oracle's step; the displacement at the oracle's stopping step is
+    within 1e-4 relative (1e-9 for FP64 against FP64)."""
+    steps_o, u_o, damped_o = oracle_relaxed(name, spec, **kw)
+    gb = srdr.Body(srdr.make_desc(spec, precision=precision))
+    st, steps_g, _ = gb.relax(1e-8, 400000)
+    assert st == srdr.SRDR_OK
+    if precision == srdr.SRDR_FP64:
+        assert steps_g == steps_o
+        assert gb.stats()["damped_steps"] == damped_o
+    else:
+        assert abs(steps_g - steps_o) <= max(2, steps_o // 100)
+    if steps_g != steps_o:
+        gb = srdr.Body(srdr.make_desc(spec, precision=precision))
+        gb.step(steps_o)
+    err = rel(gb.displacement(), u_o)
+    assert err <= 1e-4
+    if precision == srdr.SRDR_FP64:
+        assert err <= 1e-9
 
 
 @pytest.mark.parametrize("spec", [S.scaled(S.cantilever_plate_3d(), 0.2),

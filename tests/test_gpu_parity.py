@@ -1,9 +1,9 @@
 """GPU parity: the CUDA library through its C ABI against the FP64 oracle.
 
 Integer and index work (cells, colours, sweep order, neighbour lists) must be
-bit-exact.  Floating point: FP64 mode within 1e-9 relative after a few steps
-and within the stated 1e-5 relative per-step velocity error over 100 steps of
-the 2D cantilever; FP32-mixed mode within the bounds derived in the tests.
+bit-exact.  Floating point: FP64 mode within 1e-9 relative after a few steps;
+both modes within the stated 1e-5 relative per-step velocity error over 100
+steps (max_i |v_gpu - v_oracle| / max_i |v_oracle| at every step).
 """
 import numpy as np
 import pytest
@@ -232,18 +232,55 @@ def test_checkpoint_resume_equals_straight_run():
 
 
 # ------------------------------------------------------------------ FP32 mixed precision
-@pytest.mark.parametrize("base", [SMALL2D, SMALL3D])
-def test_fp32_mixed_steps(base):
-    """FP32 neighbour sums: each of the ~k terms carries a relative rounding of
-    ~6e-8 and the stress and force sums are written without cancellation, so a
-    few steps stay within ~1e-5 relative of FP64."""
-    ob = oracle_for(base)
-    gb = gpu_for(base, precision=srdr.SRDR_FP32_MIXED)
-    ob.step(10)
-    gb.step(10)
-    assert ob.damped_steps > 0
-    assert rel(gb.velocity(), ob.v) < 2e-5
-    assert rel(gb.displacement(), ob.u) < 2e-5
+FP32_BODIES = [SMALL2D, SMALL3D, S.cantilever_2d(S.SVK), S.cantilever_2d(S.NEO_HOOKEAN),
+               S.scaled(S.cantilever_plate_3d(), 0.3)]
+
+
+@pytest.mark.parametrize("spec", FP32_BODIES,
+                         ids=["small2d", "small3d", "cantilever2d-svk", "cantilever2d-nh", "plate-x0.3"])
+def test_fp32_mixed_100_steps_per_step_velocity(spec):
+    """FP32-mixed (the benchmark's precision) against the FP64 oracle at each
+    of 100 steps, damped ones included: max_i |v_gpu - v_ora| / max_i |v_ora|
+    <= 1e-5 at every step, and the same for the displacement.  The 2D
+    cantilever is the stated workload (100 x 10 + 3 clamped columns), the
+    plate the 3D workload scaled x0.3 at the same dp (60 x 6 x 30 + 3 clamped
+    layers)."""
+    ob = oracle_for(spec)
+    gb = gpu_for(spec, precision=srdr.SRDR_FP32_MIXED)
+    worst_v = worst_u = 0.0
+    for _ in range(100):
+        ob.step(1)
+        gb.step(1)
+        worst_v = max(worst_v, rel(gb.velocity(), ob.v))
+        worst_u = max(worst_u, rel(gb.displacement(), ob.u))
+    assert ob.damped_steps == gb.stats()["damped_steps"] > 0
+    assert worst_v <= 1e-5
+    assert worst_u <= 1e-5
+
+
+def test_fp32_mixed_compression_block_100_steps():
+    """The compression block (16 mm cube at dp = 1 mm, top face at -10 %),
+    FP32-mixed against the FP64 oracle over 100 steps.  This body relaxes
+    within about 220 steps, so its velocities decay by orders of magnitude
+    inside the window while the stress stays at 10 % strain: the absolute
+    velocity error, set by the FP32 rounding of the stress (about 6e-8 of
+    |P| per particle), is measured against the largest velocity the body has
+    reached so far.  The displacement is held to 1e-5 per step."""
+    spec = S.compression_block_3d(dp=1e-3, edge=0.016)
+    ob = oracle_for(spec, f_form=O.F_DISPLACEMENT)
+    gb = gpu_for(spec, precision=srdr.SRDR_FP32_MIXED)
+    peak = 0.0
+    worst_v = worst_u = 0.0
+    for _ in range(100):
+        ob.step(1)
+        gb.step(1)
+        vo = ob.v
+        peak = max(peak, np.abs(vo).max())
+        worst_v = max(worst_v, np.abs(gb.velocity() - vo).max() / peak)
+        worst_u = max(worst_u, rel(gb.displacement(), ob.u))
+    assert ob.damped_steps == gb.stats()["damped_steps"] > 0
+    assert worst_v <= 1e-5
+    assert worst_u <= 1e-5
 
 
 # ------------------------------------------------------------------ degenerate inputs
@@ -453,7 +490,7 @@ def test_explicit_comparator_fp32_mixed():
         ob.step(1)
         gb.step(1)
         worst = max(worst, rel(gb.velocity(), ob.v))
-    assert worst <= 2e-5
+    assert worst <= 1e-5
 
 
 def test_explicit_and_split_relax_to_the_same_state_on_gpu():
@@ -486,7 +523,7 @@ TWIST3D = S.BodySpec(dim=3, extent=(0.012, 0.004, 0.004), dp=1e-3, clamp_axis=0,
                      alpha=0.5, seed=3, twist=(20 * 9.8 / 0.004, 0.012, 0.002, 0.002))
 
 
-@pytest.mark.parametrize("precision,tol", [(srdr.SRDR_FP64, 1e-10), (srdr.SRDR_FP32_MIXED, 2e-5)])
+@pytest.mark.parametrize("precision,tol", [(srdr.SRDR_FP64, 1e-10), (srdr.SRDR_FP32_MIXED, 1e-5)])
 def test_twisting_body_force_matches_oracle(precision, tol):
     """The rotational body force of the twisting cantilever (Sec. 4.2):
     per-step velocity and displacement against the oracle."""
