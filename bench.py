@@ -53,6 +53,17 @@ def parse():
     ap.add_argument("--served-max-n", type=float, default=2e4)
     ap.add_argument("--served-tol", type=float, default=1e-8)
     ap.add_argument("--served-max-steps", type=int, default=20000)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-vs-one-at-a-time solves/s record of the default line")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served-stream record of the default line")
+    ap.add_argument("--batch-bodies", type=int, default=24,
+                    help="bodies of the batched solves/s sample (the first of the 256-body workload)")
+    ap.add_argument("--solve-cap", type=int, default=100000,
+                    help="step cap of the solves in the batched and served records")
+    ap.add_argument("--served-requests", type=int, default=24,
+                    help="requests per rate in the served record of the default line")
+    ap.add_argument("--served-rates", type=float, nargs="+", default=[10.0, 100.0])
     return ap.parse_args()
 
 
@@ -163,15 +174,17 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
-def oracle_rate(spec, steps, seed_steps=0):
-    """Time the FP64 oracle on `steps` steps of `spec`; returns (p-steps/s, n, seconds)."""
+def oracle_rate(spec, steps, seed_steps=0, threads=0):
+    """Time the FP64 oracle on `steps` steps of `spec` (threads > 0: its
+    OpenMP build on that many threads, the same bits); returns (p-steps/s, n,
+    seconds, damped steps)."""
     from oracle import oracle as O
     from paper_2103_08932_gb300 import synth as S
     r0, flags, u0 = S.lattice(spec)
     b = O.OracleBody(O.Params(dim=spec.dim, material=spec.material, rho0=spec.rho0, E=spec.E,
                               nu=spec.nu, h=spec.h, gravity=spec.gravity, beta=spec.beta,
                               L_char=spec.L_char, alpha=spec.alpha, seed=spec.seed),
-                     r0, vol_default=spec.vol, flags=flags)
+                     r0, vol_default=spec.vol, flags=flags, threads=threads)
     if seed_steps:
         b.step(seed_steps)
     t = time.perf_counter()
@@ -180,15 +193,43 @@ def oracle_rate(spec, steps, seed_steps=0):
     return b.n * steps / el, b.n, el, b.damped_steps
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline():
+    """The FP64 oracle on the host: its OpenMP build on every core (the
+    reported value) and its serial build on one, on the same bounded sample."""
+    from oracle import oracle as O
     from paper_2103_08932_gb300 import synth as S
     spec = S.cantilever_plate_3d()
     # bounded sample: the full 406,000-particle plate, steps 0..7 (step 7 is
-    # the first damped step of seed 1), about 10-20 s of single-thread CPU work
-    rate, n, el, damped = oracle_rate(spec, 8)
-    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"full plate ({n} particles), 8 time steps incl. {damped} damped, "
-                      f"FP64 single-thread C oracle, {el:.1f} s"}
+    # the first damped step of seed 1): about 10-20 s of single-thread work
+    cores = os.cpu_count() or 1
+    rate_all, n, el_all, damped = oracle_rate(spec, 8, threads=cores)
+    rate1, _, el1, _ = oracle_rate(spec, 8)
+    return {"value": rate_all, "unit": METRIC, "cores": O.threads_available() if cores > 1 else 1,
+            "kind": "oracle", "cpu_model": cpu_model(), "nproc": cores,
+            "single_thread_value": rate1,
+            "sample": f"full plate ({n} particles), 8 time steps incl. {damped} damped, FP64 C "
+                      f"oracle: OpenMP build on {cores} threads {el_all:.1f} s, serial build "
+                      f"{el1:.1f} s (identical bits)"}
 
 
 def run_reference(args):
@@ -198,23 +239,29 @@ def run_reference(args):
     from paper_2103_08932_gb300 import synth as S
     # each step: one oracle time step of a scaled copy of the plate (same dp,
     # same physics), sized so that W + K steps take about 90 s on one core
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    threads = cores if cores > 1 else 0
     full = S.cantilever_plate_3d()
     probe = S.scaled(full, 0.25)
-    r_probe, n_probe, _, _ = oracle_rate(probe, 2)
+    r_probe, n_probe, _, _ = oracle_rate(probe, 2, threads=threads)
     budget = 90.0 / max(1, args.steps + args.warmup)
     n_target = max(2000, min(406000, r_probe * budget))
     f = max(0.12, min(1.0, (n_target / 406000.0) ** (1.0 / 3.0)))
     spec = S.scaled(full, f)
-    rate, n, el, damped = oracle_rate(spec, args.steps, seed_steps=args.warmup)
+    rate, n, el, damped = oracle_rate(spec, args.steps, seed_steps=args.warmup, threads=threads)
     ms = el / args.steps * 1e3
+    used = O.threads_available() if threads else 1
     out = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "reference_sample": f"plate scaled x{f:.3f} ({n} particles)"},
-        "cpu_baseline": {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": rate, "unit": METRIC, "cores": used, "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": f"plate scaled x{f:.3f} ({n} particles), {args.steps} steps "
-                                   f"({damped} damped) after {args.warmup} warm-up steps"},
+                                   f"({damped} damped) after {args.warmup} warm-up steps, "
+                                   f"FP64 C oracle on {used} thread(s)"},
         "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -315,6 +362,25 @@ def run_gpu(args):
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "includes": "body build from host arrays + steps + displacement read-back"}
 
+    # per-step cost of the two kinds of step, from the per-kernel events: an
+    # undamped step is the stress and force passes; a damped step adds the
+    # damping sweep and the finish pass.  value_at_alpha is the rate at the
+    # expected damped fraction alpha = 0.2 (a short window damps a random
+    # number of steps)
+    ms_u = per["pass_a"] + per["pass_b"]
+    ms_d = ms_u + per["sweep"] + per["finish"]
+    alpha = spec.alpha
+    step_mix = {"ms_undamped_step": ms_u, "ms_damped_step": ms_d,
+                "damped_fraction": damped / args.steps, "alpha": alpha,
+                "value_at_alpha": world * n / (((1 - alpha) * ms_u + alpha * ms_d) / 1e3)}
+
+    batched = served = None
+    if rank == 0 and not args.no_batched:
+        batched = run_batched_solves(args.batch_bodies, args.solve_cap)
+    if rank == 0 and not args.no_served:
+        served = [run_served(r, args.served_requests, 1e3, 2e5, 1e-8, args.solve_cap, seed=4,
+                             workload_note=SERVED_NOTE) for r in args.served_rates]
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -334,8 +400,11 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "algorithmic_bytes": ab[dom]},
+            **step_mix,
             "kernels_ms_per_launch": per,
             "kernels_ms_total": {k: v["ms"] for k, v in kt.items()},
+            "batched": batched,
+            "served": served,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -392,7 +461,70 @@ def run_batched(nbodies, n_lo, n_hi, steps, seed=3, sync="auto"):
             "sweep_cells_per_warp": info["sweep_cells_per_warp"], "pass_threads": info["pass_threads"]}
 
 
-def run_served(rate, count, n_lo, n_hi, tol, max_steps, seed=4):
+CONFIG4_NOTE = ("random box / beam / plate bodies, particles log-uniform 1e3-2e5, aspect 1-20, "
+                "E log-uniform 1e5-1e7, nu 0.2-0.45, gravity or end load; narrowed as the "
+                "method requires: at least 6 layers thick, loads capped at a 5 % linear tip "
+                "deflection (thinner or harder-loaded bodies diverge, the oracle's too)")
+SERVED_NOTE = ("served bodies drawn like the batched workload (particles log-uniform 1e3-2e5, "
+               "not the 1e3-1e6 of the full served workload: a default run stays within minutes)")
+
+
+def run_batched_solves(nbodies, cap, tol=1e-8, seed=3):
+    """Whole solves of the batched workload's first `nbodies` bodies (FP32-mixed,
+    KE/KE_max < tol, at most `cap` steps): relaxed together as one batch, and
+    one body at a time through srdr_body_relax on the same GPU.  solves/s
+    counts converged bodies only; both runs stop every body at its own
+    criterion, so their results are bitwise the same."""
+    import torch
+
+    from paper_2103_08932_gb300 import srdr
+    from paper_2103_08932_gb300 import synth as S
+    specs = S.random_bodies(256, 1e3, 2e5, seed)[:nbodies]
+    descs = [srdr.make_desc(s, precision=srdr.SRDR_FP32_MIXED) for s in specs]
+    bodies = [srdr.Body(d) for d in descs]
+    n_total = sum(b.n for b in bodies)
+    batch = srdr.Batch(bodies)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status, per, steps_b = batch.run(tol, cap)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    info = batch.info()
+    batch.close()
+    conv_b = [int(x) == 0 for x in per]
+    u_b = [b.displacement() for b in bodies]
+    for b in bodies:
+        b.close()
+    t_alone = 0.0
+    conv_a, steps_a, same = [], [], 0
+    for k, d in enumerate(descs):
+        b = srdr.Body(d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, steps, _ = b.relax(tol, cap, check=False)
+        torch.cuda.synchronize()
+        t_alone += time.perf_counter() - t0
+        conv_a.append(st == srdr.SRDR_OK)
+        steps_a.append(steps)
+        same += int(np.array_equal(b.displacement(), u_b[k]))
+        b.close()
+    ps_b = sum(int(s) * d.n for s, d in zip(steps_b, bodies))
+    return {"workload": f"first {nbodies} bodies of the 256-body batched workload (seed {seed}; "
+                        f"{n_total} particles), FP32-mixed, KE/KE_max < {tol:g}, cap {cap} steps",
+            "bodies": CONFIG4_NOTE,
+            "converged": sum(conv_b), "not_converged": nbodies - sum(conv_b),
+            "batched_s": t_batch, "one_at_a_time_s": t_alone,
+            "batched_solves_per_s": sum(conv_b) / t_batch,
+            "one_at_a_time_solves_per_s": sum(conv_a) / t_alone,
+            "speedup": t_alone / t_batch,
+            "batched_particle_steps_per_s": ps_b / t_batch,
+            "steps_min_median_max": [int(min(steps_b)), int(np.median(steps_b)), int(max(steps_b))],
+            "bitwise_equal_to_alone": same,
+            "launches_per_step": info["launches"] / max(1, info["steps"]),
+            "sweep_cells_per_warp": info["sweep_cells_per_warp"]}
+
+
+def run_served(rate, count, n_lo, n_hi, tol, max_steps, seed=4, workload_note=None):
     """Poisson request stream of uneven bodies into the continuous-batching
     server: solves/s and p50/p99 submit-to-result latency."""
     from paper_2103_08932_gb300 import srdr
@@ -412,13 +544,19 @@ def run_served(rate, count, n_lo, n_hi, tol, max_steps, seed=4):
     statuses = [srv.wait(t, 3600.0)[0] for t in tickets]
     rep = srv.stats()
     srv.close()
-    return {"rate_per_s": rate, "requests": count,
-            "bodies": f"particles log-uniform {int(n_lo)}-{int(n_hi)}, KE/KE_max < {tol:g}, "
-                      f"cap {max_steps} steps, FP32-mixed, seed {seed}",
-            "solves_per_s": rep["solves_per_s"], "p50_latency_s": rep["p50_latency_s"],
-            "p99_latency_s": rep["p99_latency_s"], "peak_concurrent": rep["peak_concurrent"],
-            "converged": sum(1 for s in statuses if s == srdr.SRDR_OK),
-            "particle_steps_per_s": rep["particle_steps"] / max(1e-9, time.perf_counter() - t0)}
+    out = {"rate_per_s": rate, "requests": count,
+           "bodies": f"particles log-uniform {int(n_lo)}-{int(n_hi)}, KE/KE_max < {tol:g}, "
+                     f"cap {max_steps} steps, FP32-mixed, seed {seed}",
+           "solves_per_s": rep["solves_per_s"], "p50_latency_s": rep["p50_latency_s"],
+           "p99_latency_s": rep["p99_latency_s"], "peak_concurrent": rep["peak_concurrent"],
+           "converged": rep["completed"], "not_converged": rep["not_converged"],
+           "failed": rep["failed"],
+           "particle_steps_per_s": rep["particle_steps"] / max(1e-9, time.perf_counter() - t0),
+           "latency": "submit to result, converged requests only"}
+    assert out["converged"] == sum(1 for s in statuses if s == srdr.SRDR_OK)
+    if workload_note:
+        out["note"] = workload_note
+    return out
 
 
 def run_block(steps):
@@ -497,7 +635,53 @@ def run_compare(tol=1e-8, cap=200000):
                          "max_abs_displacement_m": float(np.abs(u).max())})
             b.close()
         out.append({"case": name, "tol": tol, "step_cap": cap, "runs": rows})
+    out.append(run_strength(tol, cap))
     return out
+
+
+def run_strength(tol=1e-8, cap=200000):
+    """Sec. 4.1's damping-strength comparison: eta = eta0, 5 eta0 and 10 eta0
+    (beta = 0.2, 1, 2 in Eq. viscous-parameter), each with the random choice
+    (alpha = 0.2) and damped at every step (alpha = 1), for the
+    particle-by-particle scheme (Sec. 3.1) and the pairwise scheme (Sec.
+    3.2): steps to KE/KE_max < tol, device time, and the static state reached
+    (or the divergence, reported as it happens)."""
+    import torch
+
+    from paper_2103_08932_gb300 import srdr
+    from paper_2103_08932_gb300 import synth as S
+    from dataclasses import replace
+    cases = [("2D cantilever 0.2 x 0.02 m, dp = 2 mm, neo-Hookean, FP64", S.cantilever_2d(S.NEO_HOOKEAN),
+              srdr.SRDR_FP64, (srdr.SRDR_DAMP_PARTICLE, srdr.SRDR_DAMP_PAIRWISE)),
+             ("3D plate 0.06 x 0.006 x 0.03 m, dp = 1 mm (plate scaled x0.3), FP32-mixed",
+              S.scaled(S.cantilever_plate_3d(), 0.3), srdr.SRDR_FP32_MIXED, (srdr.SRDR_DAMP_PARTICLE,))]
+    names = {srdr.SRDR_DAMP_PARTICLE: "particle-by-particle", srdr.SRDR_DAMP_PAIRWISE: "pairwise"}
+    out = []
+    for name, spec, prec, schemes in cases:
+        rows = []
+        for damping in schemes:
+            for mult in (1, 5, 10):
+                for alpha in (0.2, 1.0):
+                    b = srdr.Body(srdr.make_desc(replace(spec, beta=0.2 * mult, alpha=alpha),
+                                                 precision=prec, damping=damping))
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    status, steps, ratio = b.relax(tol, cap, check=False)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    st = b.stats()
+                    u = b.displacement()
+                    rows.append({"scheme": names[damping], "eta": f"{mult} eta0", "alpha": alpha,
+                                 "status": srdr.STATUS_NAMES.get(status, status), "steps": steps,
+                                 "dt": st["dt"], "simulated_time_s": steps * st["dt"],
+                                 "device_s": e0.elapsed_time(e1) / 1e3,
+                                 "damped_steps": st["damped_steps"],
+                                 "max_abs_displacement_m": float(np.abs(u).max())})
+                    b.close()
+        out.append({"case": name, "tol": tol, "step_cap": cap, "eta0": "beta = 0.2", "runs": rows})
+    return {"damping_strength": out}
 
 
 def main():
