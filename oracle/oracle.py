@@ -28,6 +28,7 @@ _LIB_OMP = os.path.join(_HERE, "_build", "libsrdr_oracle_omp.so")
 SVK, NEO_HOOKEAN = 0, 1
 DAMP_NONE, DAMP_PARTICLE, DAMP_PAIRWISE, DAMP_EXPLICIT = 0, 1, 2, 3
 F_RATE, F_DISPLACEMENT = 0, 1
+SWEEP_3D, SWEEP_2D = 0, 1
 FLAG_CONSTRAINED, FLAG_END_LOAD = 1, 2
 U, V, F, PB, B0, ACC = 0, 1, 2, 3, 4, 5
 
@@ -63,6 +64,7 @@ class _Params(C.Structure):
         ("damping", C.c_int), ("f_form", C.c_int),
         ("dt", C.c_double),
         ("twist", C.c_double * 4),
+        ("sweep_layout", C.c_int),
     ]
 
 
@@ -105,6 +107,7 @@ def _declare(L):
         L.ora_phi.restype = d
         L.ora_phi.argtypes = [C.c_uint64, C.c_uint64]
         L.ora_cells.argtypes = [C.c_int, i64, p, d, p, p, p, p]
+        L.ora_cells_base.argtypes = [C.c_int, i64, p, d, C.c_int, p, p, p, p]
         L.ora_neighbours_brute.restype = i64
         L.ora_neighbours_brute.argtypes = [C.c_int, i64, p, d, p, p]
         L.ora_body_create.restype = p
@@ -202,14 +205,17 @@ def phi(seed, step):
     return lib().ora_phi(seed, step)
 
 
-def cells(dim, r0, rc):
+def cells(dim, r0, rc, base=3):
     r = _vec3(r0, dim)
     n = r.shape[0]
     cell = np.zeros(n, dtype=np.int64)
     colour = np.zeros(n, dtype=np.int32)
     order = np.zeros(n, dtype=np.int64)
     nc = np.zeros(3, dtype=np.int64)
-    lib().ora_cells(dim, n, _ptr(r), rc, _ptr(cell), _ptr(colour), _ptr(nc), _ptr(order))
+    if base == 3:
+        lib().ora_cells(dim, n, _ptr(r), rc, _ptr(cell), _ptr(colour), _ptr(nc), _ptr(order))
+    else:
+        lib().ora_cells_base(dim, n, _ptr(r), rc, base, _ptr(cell), _ptr(colour), _ptr(nc), _ptr(order))
     return cell, colour, nc, order
 
 
@@ -242,6 +248,7 @@ class Params:
     f_form: int = F_RATE
     dt: float = 0.0
     twist: tuple = (0.0, 0.0, 0.0, 0.0)  # (gamma0, L, y_c, z_c), reading R17
+    sweep_layout: int = SWEEP_3D  # reading R18: SWEEP_2D = 2^d colours over cells of edge 4h
 
     def to_c(self) -> _Params:
         g = list(self.gravity) + [0.0] * (3 - len(self.gravity))
@@ -249,7 +256,7 @@ class Params:
         return _Params(self.dim, self.material, self.rho0, self.E, self.nu, self.h,
                        (C.c_double * 3)(*g), (C.c_double * 3)(*e), self.beta, self.L_char,
                        self.alpha, self.seed, self.damping, self.f_form, self.dt,
-                       (C.c_double * 4)(*self.twist))
+                       (C.c_double * 4)(*self.twist), self.sweep_layout)
 
 
 class OracleBody:

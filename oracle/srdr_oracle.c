@@ -53,6 +53,14 @@
  *       thickness H for "h" (the paper's "h" there is a length of the body, not
  *       the smoothing length).  It is added to gravity on every particle;
  *       dt's |a|max is the largest |g + end load + g_t| over the particles.
+ *   R18 2^d-colour sweep layout (ORA_SWEEP_2D, an option; Sec. 3.4 keeps the
+ *       3^d colours the default): the splitting cell-linked list with cells of
+ *       edge 2 r_c = 4h, colour sum_a (i_a mod 2) 2^a.  Same-colour cells are
+ *       then at least one cell of edge 2 r_c apart, so no particle is within
+ *       r_c of both, and the cells of a colour touch disjoint particles as in
+ *       the paper's layout.  The canonical order is colour, cell, particle id
+ *       as in R9, over these cells; it differs from the default order, so the
+ *       result of S_d differs too (another order of the same local operators).
  */
 #include "srdr_oracle.h"
 
@@ -345,6 +353,14 @@ static void cell_coords(int dim, int64_t n, const double* r0, double rc, int64_t
 void ora_cells(int dim, int64_t n, const double* r0, double rc, int64_t* cell, int* colour,
                int64_t ncell_out[3], int64_t* order)
 {
+    ora_cells_base(dim, n, r0, rc, 3, cell, colour, ncell_out, order);
+}
+
+/* The same with colour sum_a (i_a mod base) base^a (base 3: Sec. 3.4; base
+ * 2: the 2^d-colour layout of reading R18, cells of edge 2 r_c) */
+void ora_cells_base(int dim, int64_t n, const double* r0, double rc, int base, int64_t* cell,
+                    int* colour, int64_t ncell_out[3], int64_t* order)
+{
     int64_t* ic = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)(n > 0 ? n : 1));
     int64_t ncell[3];
     cell_coords(dim, n, r0, rc, ic, ncell);
@@ -352,8 +368,8 @@ void ora_cells(int dim, int64_t n, const double* r0, double rc, int64_t* cell, i
         cell[i] = ic[i * 3 + 0] + ncell[0] * (ic[i * 3 + 1] + ncell[1] * ic[i * 3 + 2]);
         int c = 0, p = 1;
         for (int a = 0; a < dim; ++a) {
-            c += (int)(ic[i * 3 + a] % 3) * p;
-            p *= 3;
+            c += (int)(ic[i * 3 + a] % base) * p;
+            p *= base;
         }
         colour[i] = c;
     }
@@ -435,6 +451,7 @@ struct ora_body {
      * colour_run[c+1]-1 */
     int64_t nrun;
     int64_t *run, *colour_run;
+    int ncolours;
     /* state */
     double *u, *v, *F, *PB, *acc;
     int64_t step;
@@ -497,15 +514,19 @@ static void build_neighbours_cll(ora_body* b)
     int64_t ncell[3];
     cell_coords(dim, n, b->r0, rc, ic, ncell);
     int64_t nc = ncell[0] * ncell[1] * ncell[2];
-    /* particles of each cell, ascending id (counting sort) */
+    /* cells of edge r_c (the search grid, whatever the sweep's layout) and
+     * their particles, ascending id (counting sort) */
+    int64_t* cid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) cid[i] = ic[i * 3 + 0] + ncell[0] * (ic[i * 3 + 1] + ncell[1] * ic[i * 3 + 2]);
     int64_t* start = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
     int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-    for (int64_t i = 0; i < n; ++i) start[b->cell[i] + 1]++;
+    for (int64_t i = 0; i < n; ++i) start[cid[i] + 1]++;
     for (int64_t c = 0; c < nc; ++c) start[c + 1] += start[c];
     int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc + 1));
     memcpy(fill, start, sizeof(int64_t) * (size_t)(nc + 1));
-    for (int64_t i = 0; i < n; ++i) list[fill[b->cell[i]]++] = i;
+    for (int64_t i = 0; i < n; ++i) list[fill[cid[i]]++] = i;
     free(fill);
+    free(cid);
 
     double c2 = rc * rc;
     int64_t cap = 64;
@@ -644,9 +665,14 @@ ora_body* ora_body_create(const ora_params* p, int64_t n, const double* r0, cons
     b->cell = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
     b->colour = (int*)malloc(sizeof(int) * (size_t)n);
     b->order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
-    ora_cells(p->dim, n, b->r0, 2.0 * p->h, b->cell, b->colour, b->ncell, b->order);
+    /* reading R18: the 2^d-colour layout takes cells of edge 2 r_c = 4h,
+     * coloured by parity; the paper's layout (Sec. 3.4) cells of edge r_c =
+     * 2h in 3^d colours */
+    b->ncolours = p->sweep_layout == ORA_SWEEP_2D ? (p->dim == 2 ? 4 : 8) : (p->dim == 2 ? 9 : 27);
+    ora_cells_base(p->dim, n, b->r0, p->sweep_layout == ORA_SWEEP_2D ? 4.0 * p->h : 2.0 * p->h,
+                   p->sweep_layout == ORA_SWEEP_2D ? 2 : 3, b->cell, b->colour, b->ncell, b->order);
     {
-        int ncol = p->dim == 2 ? 9 : 27;
+        int ncol = b->ncolours;
         b->run = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
         b->colour_run = (int64_t*)calloc((size_t)ncol + 1, sizeof(int64_t));
         int64_t r = 0;
@@ -944,7 +970,7 @@ void ora_body_damp(ora_body* b, double eta_tilde, double dt_loc)
     /* The canonical order, taken colour by colour: the runs (cells) of one
      * colour touch disjoint particles, so they may run in any order or at the
      * same time and give the serial result. */
-    int ncol = b->p.dim == 2 ? 9 : 27;
+    int ncol = b->ncolours;
     for (int c = 0; c < ncol; ++c) {
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t r = b->colour_run[c]; r < b->colour_run[c + 1]; ++r)

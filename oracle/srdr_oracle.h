@@ -33,6 +33,9 @@ enum { ORA_SVK = 0, ORA_NEO_HOOKEAN = 1 };
  * at v^n, under the explicit limit of Eq. viscous-criteria-o */
 enum { ORA_DAMP_NONE = 0, ORA_DAMP_PARTICLE = 1, ORA_DAMP_PAIRWISE = 2, ORA_DAMP_EXPLICIT = 3 };
 enum { ORA_F_RATE = 0, ORA_F_DISPLACEMENT = 1 };
+/* sweep layout: the paper's 3^d colours over cells of edge 2h (Sec. 3.4), or
+ * 2^d colours over cells of edge 4h (reading R18) */
+enum { ORA_SWEEP_3D = 0, ORA_SWEEP_2D = 1 };
 /* particle flag bits */
 enum { ORA_FLAG_CONSTRAINED = 1, ORA_FLAG_END_LOAD = 2 };
 
@@ -53,6 +56,7 @@ typedef struct {
      * rotation-body-force, reading R17): twist = (gamma0, L, y_c, z_c),
      * g_t = gamma0 sin(pi x / (2 L)) (0, -(z - z_c), y - y_c); gamma0 = 0: none */
     double twist[4];
+    int sweep_layout;      /* ORA_SWEEP_3D (default) | ORA_SWEEP_2D */
 } ora_params;
 
 /* threads of the OpenMP build (ignored by the serial build); identical bits */
@@ -78,6 +82,9 @@ double ora_phi(uint64_t seed, uint64_t step);
  * order[k] = particle id of the k-th particle in canonical sweep order. */
 void ora_cells(int dim, int64_t n, const double* r0, double rc,
                int64_t* cell, int* colour, int64_t ncell_out[3], int64_t* order);
+/* the same with colour base 3 (Sec. 3.4) or 2 (reading R18, cells of edge 4h) */
+void ora_cells_base(int dim, int64_t n, const double* r0, double rc, int base,
+                    int64_t* cell, int* colour, int64_t ncell_out[3], int64_t* order);
 
 /* ---- neighbour lists: 0 < |r0_i - r0_j| < 2h -------------------------- */
 /* brute force O(N^2).  row_ptr has n+1 entries; col has row_ptr[n] entries.
