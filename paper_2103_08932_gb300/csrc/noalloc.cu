@@ -26,10 +26,15 @@ std::mutex g_scratch_mu;
 constexpr int kMaxDevices = 128;
 double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_ke_scratch on the current device.  In host code the
-// symbol is only a host-side stand-in, so the address is looked up once per
-// device with cudaGetSymbolAddress (with that device current) and cached.
-srdr_status scratch_address(double** out)
+// Device address of g_ke_scratch in the current context.  In host code the
+// symbol is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress, with the caller's device current.  A device address
+// belongs to a context, not to a device (cudaDeviceReset, or a context the
+// caller made current through the driver API, gives another one), so every
+// call made outside stream capture looks it up again and refreshes the copy
+// kept per device ordinal; a call on a capturing stream uses that copy, which
+// is why the first call on a device must come before any capture.
+srdr_status scratch_address(cudaStream_t st, double** out)
 {
     int dev = 0;
     SRDR_CK(cudaGetDevice(&dev));
@@ -37,8 +42,10 @@ srdr_status scratch_address(double** out)
         set_error("device ordinal %d out of range", dev);
         return SRDR_ERR_INVALID;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SRDR_CK(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_ke_scratch);
         if (e != cudaSuccess || !p) {
@@ -46,6 +53,9 @@ srdr_status scratch_address(double** out)
             return SRDR_ERR_CUDA;
         }
         g_scratch_addr[dev] = static_cast<double*>(p);
+    } else if (!g_scratch_addr[dev]) {
+        set_error("first allocation-free call on device %d made during stream capture", dev);
+        return SRDR_ERR_INVALID;
     }
     *out = g_scratch_addr[dev];
     return SRDR_OK;
@@ -69,8 +79,8 @@ __global__ void __launch_bounds__(kNaThreads) k_ke_partials_na(const T* __restri
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double ke = 0.0;
     if (i < n && !(flags && (flags[i] & SRDR_FLAG_CONSTRAINED))) {
-        T vx = v[i], vy = v[n + i], vz = v[2 * n + i];
-        ke = (double)(T(0.5) * mass[i] * (vx * vx + vy * vy + vz * vz));
+        const T vi[3] = {v[i], v[n + i], v[2 * n + i]};
+        ke = ke_particle<T>(mass[i], vi);  // the per-particle term of the library's reduction
     }
     ke = na_warp_sum(ke);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -121,9 +131,9 @@ extern "C" srdr_status srdr_kinetic_energy_noalloc(const void* v, const void* ma
         set_error("unknown precision %d", precision);
         return SRDR_ERR_INVALID;
     }
-    double* scratch = nullptr;
-    SRDR_TRY(scratch_address(&scratch));
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double* scratch = nullptr;
+    SRDR_TRY(scratch_address(st, &scratch));
     const int nb = (int)((n + kNaThreads - 1) / kNaThreads);
     // every partial read below is written by this call first: nothing in the
     // scratch array has to start at zero

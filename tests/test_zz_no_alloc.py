@@ -42,7 +42,10 @@ def _ke_noalloc(L, v_soa, mass, flags, precision, out, stream=0):
     assert st == srdr.SRDR_OK, srdr.last_error()
 
 
-@pytest.mark.parametrize("precision,tol", [(srdr.SRDR_FP64, 1e-12), (srdr.SRDR_FP32_MIXED, 1e-6)])
+# each particle's term has the same roundings as the library's reduction (FP32
+# velocities and masses are passed in as the body holds them); only the order
+# of the FP64 additions differs
+@pytest.mark.parametrize("precision,tol", [(srdr.SRDR_FP64, 1e-12), (srdr.SRDR_FP32_MIXED, 1e-12)])
 def test_noalloc_kinetic_energy_matches_body_reduction(L, precision, tol):
     import torch
     spec = S.BodySpec(dim=3, extent=(0.03, 0.008, 0.012), dp=1e-3, clamp_axis=0, clamp_layers=3,
