@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sweep-sync", choices=["auto", "barrier", "cells"], default="auto",
                     help="synchronisation of the damping sweep's colour phases (default: autotuned)")
-    ap.add_argument("--workload", choices=["plate", "batched", "served", "block", "compare"],
+    ap.add_argument("--workload", choices=["plate", "batched", "served", "block", "compare", "layout"],
                     default="plate")
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000])
     ap.add_argument("--requests", type=int, default=64)
@@ -684,6 +684,41 @@ def run_strength(tol=1e-8, cap=200000):
     return {"damping_strength": out}
 
 
+def run_layout(steps=400, warmup=20):
+    """The plate with the paper's sweep layout (cells of edge r_c, 3^d = 27
+    colours, 53 colour phases per damped step) and with the 2^d layout (cells
+    of edge 2 r_c, 8 colours, 15 phases): per-kernel CUDA-event times of the
+    stress and force passes and of the sweep per damped step."""
+    import torch
+
+    from paper_2103_08932_gb300 import srdr
+    from paper_2103_08932_gb300 import synth as S
+    spec = S.cantilever_plate_3d()
+    out = {"workload": WORKLOAD, "steps": steps}
+    for name, layout in (("3d_colours", srdr.SRDR_SWEEP_LAYOUT_3D), ("2d_colours", srdr.SRDR_SWEEP_LAYOUT_2D)):
+        b = srdr.Body(srdr.make_desc(spec, precision=srdr.SRDR_FP32_MIXED, sweep_layout=layout))
+        b.step(warmup)
+        torch.cuda.synchronize()
+        b.profile(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        kt = b.kernel_times()
+        b.profile(False)
+        st = b.stats()
+        per = {k: v["ms"] / max(v["intervals"], 1) for k, v in kt.items()}
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / steps, "sweep_ms_per_damped_step": per["sweep"],
+                     "pass_a_ms": per["pass_a"], "pass_b_ms": per["pass_b"], "cells": b.ncells,
+                     "damped_steps": kt["sweep"]["intervals"],
+                     "sweep_cells_per_warp": st["sweep_cells_per_warp"],
+                     "sweep_sync": st["sweep_sync"]}
+        b.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -694,6 +729,8 @@ def main():
         print(json.dumps({"impl": "gpu", "block": run_block(args.steps)}))
     elif args.workload == "compare":
         print(json.dumps({"impl": "gpu", "compare": run_compare()}))
+    elif args.workload == "layout":
+        print(json.dumps({"impl": "gpu", "layout": run_layout(args.steps, args.warmup)}))
     elif args.workload == "served":
         out = [run_served(r, args.requests, 1e3, args.served_max_n, args.served_tol,
                           args.served_max_steps) for r in args.rates]

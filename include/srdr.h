@@ -52,6 +52,7 @@ enum { SRDR_LINEAR_SVK = 0, SRDR_NEO_HOOKEAN = 1 };
 enum { SRDR_FP64 = 0, SRDR_FP32_MIXED = 1 };
 enum { SRDR_DAMP_NONE = 0, SRDR_DAMP_PARTICLE = 1, SRDR_DAMP_PAIRWISE = 2, SRDR_DAMP_EXPLICIT = 3 };
 enum { SRDR_FLAG_CONSTRAINED = 1, SRDR_FLAG_END_LOAD = 2 };
+enum { SRDR_SWEEP_LAYOUT_3D = 0, SRDR_SWEEP_LAYOUT_2D = 1 };
 
 /*
  * Body description (POD, caller-owned, copied by the create calls).
@@ -90,6 +91,17 @@ enum { SRDR_FLAG_CONSTRAINED = 1, SRDR_FLAG_END_LOAD = 2 };
  *   (0, -(z - twist[3]), y - twist[2]) per unit mass, x from the clamped face
  *   (the printed (0, y gamma, z gamma) is radial, not rotational).  Added to
  *   gravity on every particle; 3D only; twist[0] = 0: none.
+ * sweep_layout: the splitting cell-linked list that orders the damping sweep
+ *   (Sec. 3.4).  SRDR_SWEEP_LAYOUT_3D (0, the paper's): cells of edge
+ *   r_c = 2h in 3^d colours, colour sum_a (i_a mod 3) 3^a.
+ *   SRDR_SWEEP_LAYOUT_2D: cells of edge 2 r_c in 2^d colours, colour
+ *   sum_a (i_a mod 2) 2^a; same-colour cells are still a cell of edge 2 r_c
+ *   apart, so no particle is within r_c of two of them and they commute.
+ *   Fewer colour phases (2^(d+1) - 1 instead of 2 3^d - 1) of cells 2^d times
+ *   larger; the sweep order, and so the damped velocities, differ from the
+ *   paper's layout within the method (the same static state).  The stress and
+ *   force passes do not depend on it.  Batches refuse these bodies, and the
+ *   sweep's footprint must fit in shared memory (FP64 3D does not).
  */
 typedef struct {
     int dim;
@@ -111,6 +123,7 @@ typedef struct {
     int precision;
     double dt;
     double twist[4];
+    int sweep_layout;
 } srdr_body_desc;
 
 typedef struct srdr_body srdr_body;
@@ -231,7 +244,7 @@ srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp, int sweep_
  * barriers otherwise.  A batch uses the mode all of its bodies ask for, else
  * its own autotuner's choice.
  * Results are bitwise the same under every choice.  Every wait is bounded
- * (one second); a sweep whose wait runs out sets the body's status, and
+ * (five seconds); a sweep whose wait runs out sets the body's status, and
  * srdr_body_relax returns SRDR_ERR_TIMEOUT after resetting the
  * synchronisation words (the velocity state is then that of a partial sweep:
  * restore it with srdr_body_write_state).  Returns SRDR_ERR_INVALID for
@@ -242,7 +255,7 @@ srdr_status srdr_body_sweep_sync(srdr_body* body, int mode);
 /* Test hook of the failure path above: makes every wait of the body's next
  * damping sweep run out (it sets the synchronisation words to counts that no
  * cell reaches), so that the sweep ends with the body's status set after
- * about a second.  Nothing else changes; the next srdr_body_relax reports
+ * about five seconds.  Nothing else changes; the next srdr_body_relax reports
  * SRDR_ERR_TIMEOUT and resets the words. */
 srdr_status srdr_body_debug_stall_sweep(srdr_body* body);
 
@@ -294,6 +307,22 @@ srdr_status srdr_batch_step(srdr_batch* batch, int64_t nsteps);
  * non-OK per-body status, or SRDR_ERR_TIMEOUT if a grid barrier gave up. */
 srdr_status srdr_batch_run(srdr_batch* batch, double ke_ratio, int64_t max_steps,
                            srdr_status* per_body_status, int64_t* per_body_steps);
+/* How a batch runs its bodies' steps.
+ * SRDR_BATCH_SHARED: the shared launches described above (one stress pass,
+ * one force pass, one colour-synchronised sweep ... per step for all bodies).
+ * SRDR_BATCH_STREAMS: every body runs its own step kernels (those of
+ * srdr_body_step, graph replays for small bodies) on one of up to 64 streams
+ * of the batch, all bodies at the same time, in chunks of steps after which
+ * the host retires the bodies that met their criterion.  A damped step's
+ * sweep is a chain of dependent colour phases (Sec. 3.4) about as long for a
+ * small body as for a large one; concurrent bodies overlap these chains,
+ * where shared launches make every body wait at every step for the slowest
+ * damped body.  SRDR_BATCH_AUTO (the default) is SRDR_BATCH_STREAMS, measured
+ * faster on GB300 (2x to 4.5x on uneven bodies).  Results are bitwise the same
+ * in every mode and equal to the bodies relaxed alone.  SRDR_ERR_INVALID for
+ * another mode. */
+enum { SRDR_BATCH_AUTO = 0, SRDR_BATCH_SHARED = 1, SRDR_BATCH_STREAMS = 2 };
+srdr_status srdr_batch_mode(srdr_batch* batch, int mode);
 /* Steps run, kernels launched, and the autotuner's choices (damping-sweep
  * cells per warp, threads per block of the passes); any may be NULL. */
 srdr_status srdr_batch_info(const srdr_batch* batch, int64_t* steps, int64_t* launches,
@@ -372,9 +401,13 @@ const char* srdr_last_error(void);
  * The scratch space is a fixed array of 16384 FP64 partial sums (128 KiB)
  * compiled into the library; every GPU that loads the library holds it until
  * the process exits.  One partial covers 256 particles, so n may be at most
- * 4,194,304; larger n returns SRDR_ERR_INVALID.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress with that
- * device current); make that first call before any stream capture.  All calls
+ * 4,194,304; larger n returns SRDR_ERR_INVALID.  Every call made outside
+ * stream capture looks up the array's device address in the current context
+ * (cudaGetSymbolAddress; the address changes with the context, e.g. after
+ * cudaDeviceReset); a call on a capturing stream reuses the address of the
+ * last call on that device outside capture, so make the first call on each
+ * device before any stream capture.  Each particle's term 1/2 m |v|^2 is
+ * rounded as in the library's own reduction.  All calls
  * share the one array: calls whose GPU work overlaps (different streams, or
  * different host threads on one device) race and may return wrong sums, so
  * order them on one stream.  Each call writes every partial it reads before

@@ -129,6 +129,10 @@ srdr_status check_desc(const srdr_body_desc* d)
         set_error("the twisting body force needs dim 3, a finite amplitude and axis, and L > 0");
         return SRDR_ERR_INVALID;
     }
+    if (d->sweep_layout != SRDR_SWEEP_LAYOUT_3D && d->sweep_layout != SRDR_SWEEP_LAYOUT_2D) {
+        set_error("unknown sweep layout %d", d->sweep_layout);
+        return SRDR_ERR_INVALID;
+    }
     return SRDR_OK;
 }
 
@@ -208,7 +212,11 @@ srdr_status create_common(const srdr_body_desc* desc, int64_t n, const double* r
     b->prec = desc->precision;
     b->stream = static_cast<cudaStream_t>(stream);
     b->h = desc->h_over_dp * desc->dp;
-    b->rc = 2.0 * b->h;
+    b->cut = 2.0 * b->h;
+    // the splitting cell-linked list: cells of edge r_c in 3^d colours (Sec.
+    // 3.4), or of edge 2 r_c in 2^d colours (SRDR_SWEEP_LAYOUT_2D)
+    b->cbase = desc->sweep_layout == SRDR_SWEEP_LAYOUT_2D ? 2 : 3;
+    b->rc = desc->sweep_layout == SRDR_SWEEP_LAYOUT_2D ? 2.0 * b->cut : b->cut;
     b->vol0 = b->dim == 2 ? desc->dp * desc->dp : desc->dp * desc->dp * desc->dp;
     lame(desc->E, desc->nu, &b->lambda, &b->mu);
     b->eta = 0.25 * desc->beta * sqrt(desc->rho0 * desc->E) * desc->L_char;
@@ -659,6 +667,10 @@ srdr_status srdr_body_pass_mapping(srdr_body* b, int mapping, int bx, int by, in
         set_error("pass mapping must be SRDR_PASS_AUTO, _SELL or _BRICKS with brick sizes 0..4");
         return SRDR_ERR_INVALID;
     }
+    if (mapping == SRDR_PASS_BRICKS && b->desc.sweep_layout != SRDR_SWEEP_LAYOUT_3D) {
+        set_error("brick-tiled passes need the 3^d-colour sweep layout (bricks of cells of edge r_c)");
+        return SRDR_ERR_INVALID;
+    }
     const bool resize = bx != b->brick[0] || by != b->brick[1] || bz != b->brick[2];
     if (resize && b->bricks_built != 0) {
         // drop the old layout; the next step that needs bricks rebuilds it
@@ -759,8 +771,9 @@ srdr_status srdr_body_read_cells(const srdr_body* b, int64_t* cell, int* colour,
     SRDR_CK(cudaMemcpy(perm.data(), b->perm, sizeof(int) * n, cudaMemcpyDeviceToHost));
     SRDR_CK(cudaMemcpy(inv.data(), b->inv, sizeof(int) * n, cudaMemcpyDeviceToHost));
     auto col_of = [&](int c) {
+        const int q = b->cbase;
         int cx = c % b->nc[0], cy = (c / b->nc[0]) % b->nc[1], cz = c / (b->nc[0] * b->nc[1]);
-        return cx % 3 + (b->dim >= 2 ? 3 * (cy % 3) : 0) + (b->dim >= 3 ? 9 * (cz % 3) : 0);
+        return cx % q + (b->dim >= 2 ? q * (cy % q) : 0) + (b->dim >= 3 ? q * q * (cz % q) : 0);
     };
     for (int i = 0; i < n; ++i) {
         cell[i] = cof[inv[i]];

@@ -343,6 +343,10 @@ struct srdr_batch {
     int graph_steps = 0;
     int graphs_ok = 1;
     std::vector<void*> allocs;
+    // SRDR_BATCH_STREAMS: each body steps with its own kernels on one of
+    // these streams, all bodies at once
+    int mode = SRDR_BATCH_AUTO;
+    std::vector<cudaStream_t> pool;
 };
 
 namespace srdr {
@@ -388,6 +392,7 @@ SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
     s.row_ptr = b->row_ptr;
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
+    s.rec = static_cast<const SweepSlot<T>*>(b->srec);
     s.mass = static_cast<const T*>(b->mass);
     s.sbm = static_cast<const T*>(b->sbm);
     s.srd = static_cast<const T*>(b->srd);
@@ -395,6 +400,11 @@ SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
     s.sc = b->sc;
     s.c = b->desc.alpha > 0 ? (T)(b->eta / b->desc.alpha * b->dt) : T(0);
     s.pairwise = b->desc.damping == SRDR_DAMP_PAIRWISE;
+    s.cbase = b->cbase;
+    s.wrad = b->cbase == 3 ? 2 : 1;
+    s.foot_ptr = b->foot_ptr;
+    s.foot_tab = b->foot_tab;
+    s.own_off = b->own_off;
     s.max_foot = F;  // one shared-memory layout for the whole batch
     s.max_pairs = P;
     s.max_cell = C;
@@ -784,8 +794,113 @@ srdr_status batch_dispatch(srdr_batch* bt, int64_t nsteps, double tol, srdr_stat
     return batch_steps<T, 3>(bt, nsteps, tol, 4096, st, steps);
 }
 
+// Concurrent mode: every body runs its own step kernels (srdr_body_step's,
+// graph replays for small bodies) on one of a pool of streams, all bodies at
+// once, in chunks of steps; after each chunk the host reads each body's
+// scalars and retires the ones that met their criterion.  A damped step's
+// sweep is a chain of dependent colour phases whose length does not shrink
+// with the body; bodies on different streams overlap those chains instead of
+// waiting for each other's at every step, as shared launches must.  Each
+// body's kernels and their order are those of srdr_body_relax, so its result
+// is bitwise the same as alone.
+constexpr int kPoolStreams = 64;
+
+srdr_status batch_run_streams(srdr_batch* bt, int64_t nsteps, double tol, srdr_status* per_status,
+                              int64_t* per_steps)
+{
+    const int nb = (int)bt->bodies.size();
+    const int ns = std::min(nb, kPoolStreams);
+    while ((int)bt->pool.size() < ns) {
+        cudaStream_t q = nullptr;
+        SRDR_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+        bt->pool.push_back(q);
+    }
+    std::vector<cudaStream_t> saved(nb);
+    std::vector<int64_t> start(nb);
+    for (int b = 0; b < nb; ++b) {
+        srdr_body* body = bt->bodies[b];
+        SRDR_CK(cudaStreamSynchronize(body->stream));  // the body's earlier work first
+        saved[b] = body->stream;
+        body->stream = bt->pool[b % ns];
+        start[b] = body->step;
+    }
+    srdr_status result = SRDR_OK;
+    std::vector<int> live;
+    for (int b = 0; b < nb; ++b) {
+        srdr_status r = reset_scalars(bt->bodies[b], tol);
+        if (r != SRDR_OK && result == SRDR_OK) result = r;
+        live.push_back(b);
+    }
+    int64_t left = nsteps, chunk = 64;
+    while (result == SRDR_OK && left > 0 && !live.empty()) {
+        const int64_t k = std::min(left, chunk);
+        for (int b : live) {
+            srdr_body* body = bt->bodies[b];
+            srdr_status r = launch_steps(body, k);
+            if (r == SRDR_OK && cudaMemcpyAsync(body->sc_host, body->sc, sizeof(DevScalars),
+                                                cudaMemcpyDeviceToHost, body->stream) != cudaSuccess) {
+                set_error("reading the scalars of a batched body failed");
+                r = SRDR_ERR_CUDA;
+            }
+            if (r != SRDR_OK) {
+                result = r;
+                break;
+            }
+        }
+        std::vector<int> keep;
+        for (int b : live) {
+            srdr_body* body = bt->bodies[b];
+            if (cudaStreamSynchronize(body->stream) != cudaSuccess) {
+                set_error("a batched body's stream failed: %s", cudaGetErrorString(cudaGetLastError()));
+                if (result == SRDR_OK) result = SRDR_ERR_CUDA;
+                continue;
+            }
+            body->step = body->sc_host->step;
+            if (body->sc_host->status == DEV_TIMEOUT) {
+                reset_sync_words(body);
+                set_error("a bounded wait of a batched body's damping sweep ran out");
+                if (result == SRDR_OK) result = SRDR_ERR_TIMEOUT;
+                continue;
+            }
+            if (!(tol > 0 && body->sc_host->done) && body->sc_host->status != DEV_NONFINITE) keep.push_back(b);
+        }
+        live.swap(keep);
+        left -= k;
+        bt->steps += k;
+        chunk = std::min<int64_t>(chunk * 2, 4096);
+    }
+    for (int b = 0; b < nb; ++b) {
+        srdr_body* body = bt->bodies[b];
+        if (cudaMemcpyAsync(body->sc_host, body->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                            body->stream) == cudaSuccess)
+            cudaStreamSynchronize(body->stream);
+        const DevScalars& s = *body->sc_host;
+        body->step = s.step;
+        body->converged = s.done && s.status == DEV_OK && tol > 0;
+        if (per_steps) per_steps[b] = s.step - start[b];
+        if (per_status) {
+            if (s.status == DEV_NONFINITE) per_status[b] = SRDR_ERR_NONFINITE;
+            else if (tol > 0 && !s.done) per_status[b] = SRDR_ERR_NOT_CONVERGED;
+            else per_status[b] = SRDR_OK;
+        }
+        reset_scalars(body, 0.0);
+        cudaStreamSynchronize(body->stream);
+        body->stream = saved[b];
+    }
+    return result;
+}
+
 srdr_status batch_run(srdr_batch* bt, int64_t nsteps, double tol, srdr_status* st, int64_t* steps)
 {
+    if (bt->mode != SRDR_BATCH_SHARED) {
+        std::vector<int64_t> l0(bt->bodies.size());
+        for (size_t b = 0; b < bt->bodies.size(); ++b) l0[b] = bt->bodies[b]->launches;
+        const int64_t before = bt->launches;
+        srdr_status r = batch_run_streams(bt, nsteps, tol, st, steps);
+        bt->launches = before;
+        for (size_t b = 0; b < bt->bodies.size(); ++b) bt->launches += bt->bodies[b]->launches - l0[b];
+        return r;
+    }
     if (bt->prec == SRDR_FP64) return batch_dispatch<double>(bt, nsteps, tol, st, steps);
     return batch_dispatch<float>(bt, nsteps, tol, st, steps);
 }
@@ -798,6 +913,10 @@ void batch_free(srdr_batch* bt)
     for (void* p : bt->allocs) cudaFree(p);
     if (bt->gathered_h) cudaFreeHost(bt->gathered_h);
     if (bt->owns_stream && bt->stream) cudaStreamDestroy(bt->stream);
+    for (cudaStream_t q : bt->pool) {
+        cudaStreamSynchronize(q);
+        cudaStreamDestroy(q);
+    }
     if (bt->owns_bodies)
         for (srdr_body* b : bt->bodies) srdr_body_destroy(b);
     delete bt;
@@ -812,9 +931,10 @@ srdr_status batch_create(srdr_body* const* bodies, int nb, void* stream, bool ow
     *out = nullptr;
     for (int b = 0; b < nb; ++b)
         if (!bodies[b] || bodies[b]->dim != bodies[0]->dim || bodies[b]->prec != bodies[0]->prec ||
-            bodies[b]->desc.damping == SRDR_DAMP_EXPLICIT) {
-            set_error("batched bodies must all exist, share dimension and precision, and use "
-                      "split damping or none");
+            bodies[b]->desc.damping == SRDR_DAMP_EXPLICIT ||
+            bodies[b]->desc.sweep_layout != SRDR_SWEEP_LAYOUT_3D) {
+            set_error("batched bodies must all exist, share dimension and precision, use "
+                      "split damping or none, and the paper's 3^d-colour sweep layout");
             return SRDR_ERR_INVALID;
         }
     srdr_batch* bt = new (std::nothrow) srdr_batch();
@@ -917,6 +1037,16 @@ srdr_status srdr_batch_run(srdr_batch* bt, double ke_ratio, int64_t max_steps,
     if (per_body_status)
         for (size_t b = 0; b < bt->bodies.size(); ++b)
             if (per_body_status[b] != SRDR_OK) return per_body_status[b];
+    return SRDR_OK;
+}
+
+srdr_status srdr_batch_mode(srdr_batch* bt, int mode)
+{
+    if (!bt || mode < SRDR_BATCH_AUTO || mode > SRDR_BATCH_STREAMS) {
+        set_error("batch mode must be SRDR_BATCH_AUTO, _SHARED or _STREAMS");
+        return SRDR_ERR_INVALID;
+    }
+    bt->mode = mode;
     return SRDR_OK;
 }
 

@@ -353,33 +353,34 @@ __global__ void k_v_init(int n, const T* __restrict__ minv, T* __restrict__ v)
     v[(size_t)i * 4 + 3] = minv[i];
 }
 
-// colour = sum_a (i_a mod 3) 3^a, per non-empty cell
-__device__ inline int cell_colour(int c, int dim, int nx, int ny)
+// colour = sum_a (i_a mod q) q^a per non-empty cell: q = 3 (Sec. 3.4) or
+// q = 2 (the 2^d layout over cells of edge 2 r_c)
+__device__ inline int cell_colour(int c, int dim, int nx, int ny, int q)
 {
     int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-    int col = cx % 3;
-    if (dim >= 2) col += 3 * (cy % 3);
-    if (dim >= 3) col += 9 * (cz % 3);
+    int col = cx % q;
+    if (dim >= 2) col += q * (cy % q);
+    if (dim >= 3) col += q * q * (cz % q);
     return col;
 }
 
-__global__ void k_colour_count(const int* __restrict__ start, int ncells, int dim, int nx, int ny,
+__global__ void k_colour_count(const int* __restrict__ start, int ncells, int dim, int nx, int ny, int q,
                                int* __restrict__ ccount)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     if (start[c + 1] == start[c]) return;
-    atomicAdd(&ccount[cell_colour(c, dim, nx, ny)], 1);
+    atomicAdd(&ccount[cell_colour(c, dim, nx, ny, q)], 1);
 }
 
-__global__ void k_colour_fill(const int* __restrict__ start, int ncells, int dim, int nx, int ny,
+__global__ void k_colour_fill(const int* __restrict__ start, int ncells, int dim, int nx, int ny, int q,
                               const int* __restrict__ cptr, int* __restrict__ cfill,
                               int* __restrict__ ccells)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     if (start[c + 1] == start[c]) return;
-    int col = cell_colour(c, dim, nx, ny);
+    int col = cell_colour(c, dim, nx, ny, q);
     ccells[cptr[col] + atomicAdd(&cfill[col], 1)] = c;
 }
 
@@ -614,6 +615,54 @@ __global__ void k_sell_fill(int n, const int* __restrict__ row_ptr, const int* _
     }
 }
 
+// sliced ELL of the FP32 3D passes: per slot the neighbour and its packed
+// pair gradient (gq_encode with the row's unit, the same formula as above
+// before packing), per row the unit, and G_i summed in FP64 in row order
+// from the decoded values (replacing k_gsum's), so the force sum's
+// difference form holds for the values the passes read
+__global__ void k_sell_fill_packed(int n, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                                   const int* __restrict__ sell_ptr, const float* __restrict__ cpos,
+                                   const int* __restrict__ ccell, float rc, float inv_h, float kc,
+                                   int* __restrict__ scol, unsigned long long* __restrict__ sgq,
+                                   float* __restrict__ gunit, float* __restrict__ Gs)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = i >> 5, lane = i & 31;
+    int base = sell_ptr[s], width = (sell_ptr[s + 1] - base) >> 5;
+    int k0 = row_ptr[i], deg = row_ptr[i + 1] - k0;
+    const vec4_t<float> pi = load_cpos<float>(cpos, i);
+    const int ci = ccell[i];
+    float mx = 0.f;
+    for (int t = 0; t < deg; ++t) {
+        const int j = col[k0 + t];
+        float gg[3];
+        PairG<float>::template g<3>(pi, ci, load_cpos<float>(cpos, j), ccell[j], rc, inv_h, kc, gg);
+        for (int q = 0; q < 3; ++q) mx = fmaxf(mx, fabsf(gg[q]));
+    }
+    int e = 0;
+    frexpf(mx, &e);  // mx = f 2^e, 1/2 <= f < 1: every |component| < 2^e
+    const float unit = ldexpf(1.f, e - 20), inv = ldexpf(1.f, 20 - e);
+    double G[3] = {0, 0, 0};
+    for (int t = 0; t < width; ++t) {
+        const int64_t slot = (int64_t)base + t * 32 + lane;
+        unsigned long long w = 0;
+        int j = i;
+        if (t < deg) {
+            j = col[k0 + t];
+            float gg[3], d[3];
+            PairG<float>::template g<3>(pi, ci, load_cpos<float>(cpos, j), ccell[j], rc, inv_h, kc, gg);
+            w = gq_encode(gg, inv);
+            gq_decode(w, unit, d);
+            for (int q = 0; q < 3; ++q) G[q] += (double)d[q];
+        }
+        scol[slot] = j;
+        sgq[slot] = w;
+    }
+    gunit[i] = unit;
+    for (int q = 0; q < 3; ++q) Gs[(size_t)q * n + i] = (float)G[q];
+}
+
 __global__ void k_foot_stats(const int* __restrict__ start, int ncells, int dim, int nx, int ny,
                              int nz, const int* __restrict__ row_ptr, int* __restrict__ out)
 {
@@ -625,6 +674,77 @@ __global__ void k_foot_stats(const int* __restrict__ start, int ncells, int dim,
     atomicMax(&out[0], foot);
     atomicMax(&out[1], row_ptr[b] - row_ptr[a]);
     atomicMax(&out[2], b - a);
+}
+
+// 2^d layout: the particles a cell's sweep touches (its own particles and
+// their neighbours), as ranks among the positions of its 3^d-cell footprint.
+// One block per cell of the grid.  fill = 0 counts them (and their maximum);
+// fill = 1 rewrites the cell's row entries' footprint-local indices into
+// ranks, stores the touched particles' sorted indices at foot_tab[foot_ptr[c]
+// + rank] (ascending: footprint positions follow the sorted order) and the
+// rank of the cell's first particle.  Shared memory: one flag and one rank
+// per footprint position (maxf of them).
+__global__ void __launch_bounds__(256) k_touch(const int* __restrict__ start, int dim, int nx, int ny, int nz,
+                                               const int* __restrict__ row_ptr, uint16_t* __restrict__ loc,
+                                               int maxf, int fill, int* __restrict__ count,
+                                               int* __restrict__ maxcount, const int* __restrict__ foot_ptr,
+                                               int* __restrict__ foot_tab, int* __restrict__ own_off)
+{
+    extern __shared__ int tsm[];
+    int* rank = tsm;                  // [maxf]
+    int* part = tsm + maxf;           // [256] per-thread counts
+    const int c = blockIdx.x;
+    const int cs = start[c], ce = start[c + 1];
+    if (cs == ce) return;
+    int a_r[9], off_r[10], nr = 0;
+    int own = 0;
+    const int F = for_footprint(c, dim, nx, ny, nz, start, [&](int a, int b, int off) {
+        if (cs >= a && cs < b) own = off + (cs - a);
+        a_r[nr] = a;
+        off_r[nr] = off;
+        ++nr;
+    });
+    off_r[nr] = F;
+    for (int f = threadIdx.x; f < F; f += blockDim.x) rank[f] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < ce - cs; q += blockDim.x) rank[own + q] = 1;
+    for (int k = row_ptr[cs] + threadIdx.x; k < row_ptr[ce]; k += blockDim.x) rank[loc[k]] = 1;
+    __syncthreads();
+    // exclusive scan of the flags: each thread a contiguous chunk
+    const int chunk = (F + blockDim.x - 1) / blockDim.x;
+    const int f0 = min(F, (int)threadIdx.x * chunk), f1 = min(F, f0 + chunk);
+    int cnt = 0;
+    for (int f = f0; f < f1; ++f) cnt += rank[f];
+    part[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int x = part[t];
+            part[t] = run;
+            run += x;
+        }
+        if (!fill) {
+            count[c] = run;
+            atomicMax(maxcount, run);
+        }
+    }
+    __syncthreads();
+    if (!fill) return;
+    int run = part[threadIdx.x];
+    for (int f = f0; f < f1; ++f) {
+        const int flag = rank[f];
+        rank[f] = flag ? run : -1;
+        if (flag) {
+            int r = 0;
+            while (r + 1 < nr && f >= off_r[r + 1]) ++r;
+            foot_tab[foot_ptr[c] + run] = a_r[r] + (f - off_r[r]);
+        }
+        run += flag;
+    }
+    __syncthreads();
+    for (int k = row_ptr[cs] + threadIdx.x; k < row_ptr[ce]; k += blockDim.x) loc[k] = (uint16_t)rank[loc[k]];
+    if (threadIdx.x == 0) own_off[c] = rank[own];
 }
 
 srdr_status scan_exclusive(const int* in, int* out, int count, int* tmp, cudaStream_t st)
@@ -740,7 +860,7 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_CK(cudaGetLastError());
 
     // colour split: non-empty cells grouped by colour
-    b->ncolours = dim == 2 ? 9 : 27;
+    b->ncolours = b->cbase == 3 ? (dim == 2 ? 9 : 27) : (dim == 2 ? 4 : 8);
     int *ccount = nullptr, *cfill = nullptr, *cptr = nullptr;
     SRDR_TRY(dalloc(b, &ccount, 27));
     SRDR_TRY(dalloc(b, &cfill, 27));
@@ -749,7 +869,7 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_CK(cudaMemsetAsync(ccount, 0, sizeof(int) * 27, st));
     SRDR_CK(cudaMemsetAsync(cfill, 0, sizeof(int) * 27, st));
     k_colour_count<<<nblocks(ncells), kThreads, 0, st>>>(b->cell_start, ncells, dim, g.nx, g.ny,
-                                                         ccount);
+                                                         b->cbase, ccount);
     int hcount[27];
     SRDR_CK(cudaMemcpyAsync(hcount, ccount, sizeof(hcount), cudaMemcpyDeviceToHost, st));
     SRDR_CK(cudaStreamSynchronize(st));
@@ -760,13 +880,13 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     SRDR_CK(cudaMemcpyAsync(cptr, b->colour_ptr.data(), sizeof(int) * (b->ncolours + 1),
                             cudaMemcpyHostToDevice, st));
     k_colour_fill<<<nblocks(ncells), kThreads, 0, st>>>(b->cell_start, ncells, dim, g.nx, g.ny,
-                                                        cptr, cfill, b->colour_cells);
+                                                        b->cbase, cptr, cfill, b->colour_cells);
 
     // neighbour CSR
     int* deg = nullptr;
     SRDR_TRY(dalloc(b, &deg, n));
     SRDR_TRY(dalloc(b, &b->row_ptr, (size_t)n + 1));
-    double rc2 = b->rc * b->rc;
+    double rc2 = b->cut * b->cut;  // the neighbour cut-off (the cell edge rc may be larger)
     float4* pof = nullptr;
     SRDR_TRY(dalloc(b, &pof, n));
     SRDR_TRY(dalloc(b, &b->ccell, n));
@@ -838,17 +958,27 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
         return SRDR_ERR_INVALID;
     }
     b->nslots = nslots;
-    T* sg = nullptr;
     const int64_t ns = std::max(nslots, 1);
     SRDR_TRY(dalloc(b, &b->sell_col, ns));
-    SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
-    b->sell_g = sg;
-    if (dim == 2)
-        k_sell_fill<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
-                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
-    else
-        k_sell_fill<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
-                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
+    if (sizeof(T) == 4 && dim == 3) {
+        // FP32 3D: packed pair gradients, 8 bytes a slot instead of 12
+        SRDR_TRY(dalloc(b, &b->sell_gq, ns));
+        SRDR_TRY(dalloc(b, &b->gunit, n));
+        k_sell_fill_packed<<<nblocks(n), kThreads, 0, st>>>(
+            n, b->row_ptr, b->col, b->sell_ptr, reinterpret_cast<const float*>(cpos), b->ccell,
+            (float)b->rc, (float)(1.0 / b->h), (float)kernel_kc(dim, b->h), b->sell_col, b->sell_gq,
+            b->gunit, reinterpret_cast<float*>(Gs));
+    } else {
+        T* sg = nullptr;
+        SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
+        b->sell_g = sg;
+        if (dim == 2)
+            k_sell_fill<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos,
+                                                               b->ccell, rcT, ihT, kcT, b->sell_col, sg, ns);
+        else
+            k_sell_fill<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos,
+                                                               b->ccell, rcT, ihT, kcT, b->sell_col, sg, ns);
+    }
 
     // footprint maxima size the damping sweep's shared memory
     int* fs = nullptr;
@@ -863,6 +993,50 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     b->max_foot = hfs[0];
     b->max_pairs = hfs[1];
     b->max_cell = hfs[2];
+    if (b->max_foot >= 65536) {
+        set_error("a cell footprint holds %d particles (limit 65535)", b->max_foot);
+        return SRDR_ERR_INVALID;
+    }
+    if (b->cbase == 2) {
+        // 2^d layout: the sweep stages only the particles each cell touches
+        // (same-colour cells' 3^d footprints overlap; what they touch does not)
+        const size_t tsm = sizeof(int) * ((size_t)b->max_foot + 256);
+        if (tsm > 200 * 1024) {
+            set_error("a cell footprint of %d particles is too large for the 2^d sweep layout", b->max_foot);
+            return SRDR_ERR_INVALID;
+        }
+        if (tsm > 48 * 1024)
+            SRDR_CK(cudaFuncSetAttribute((const void*)k_touch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tsm));
+        int *tcount = nullptr, *tmax = nullptr;
+        SRDR_TRY(dalloc(b, &tcount, ncells));
+        SRDR_TRY(dalloc(b, &tmax, 1));
+        SRDR_TRY(dalloc(b, &b->foot_ptr, (size_t)ncells + 1));
+        SRDR_TRY(dalloc(b, &b->own_off, ncells));
+        SRDR_CK(cudaMemsetAsync(tcount, 0, sizeof(int) * ncells, st));
+        SRDR_CK(cudaMemsetAsync(tmax, 0, sizeof(int), st));
+        SRDR_CK(cudaMemsetAsync(b->own_off, 0, sizeof(int) * ncells, st));
+        k_touch<<<ncells, 256, tsm, st>>>(b->cell_start, dim, g.nx, g.ny, g.nz, b->row_ptr, b->loc,
+                                          b->max_foot, 0, tcount, tmax, nullptr, nullptr, nullptr);
+        SRDR_TRY(scan_exclusive(tcount, b->foot_ptr, ncells, tmp, st));
+        int total = 0, mx = 0;
+        SRDR_CK(cudaMemcpyAsync(&total, b->foot_ptr + ncells, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SRDR_CK(cudaMemcpyAsync(&mx, tmax, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SRDR_CK(cudaStreamSynchronize(st));
+        if (total < 0) {
+            set_error("touched lists of the 2^d sweep layout exceed 2^31 entries");
+            return SRDR_ERR_INVALID;
+        }
+        SRDR_TRY(dalloc(b, &b->foot_tab, std::max(total, 1)));
+        k_touch<<<ncells, 256, tsm, st>>>(b->cell_start, dim, g.nx, g.ny, g.nz, b->row_ptr, b->loc,
+                                          b->max_foot, 1, tcount, tmax, b->foot_ptr, b->foot_tab,
+                                          b->own_off);
+        SRDR_CK(cudaGetLastError());
+        SRDR_CK(cudaStreamSynchronize(st));
+        SRDR_TRY(dev_free(b, tcount));
+        SRDR_TRY(dev_free(b, tmax));
+        b->max_foot = mx;
+    }
     SRDR_TRY(dalloc(b, &b->bar, kBarWords));
     SRDR_CK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * kBarWords, st));
     SRDR_TRY(dalloc(b, &b->flow, flow_words(ncells)));
@@ -1045,7 +1219,9 @@ __global__ void k_bsell_fill(const BrickInfo* __restrict__ info, const int* __re
                              const int* __restrict__ col, const int* __restrict__ cell_of,
                              const int* __restrict__ bsell_ptr, const T* __restrict__ cpos,
                              const int* __restrict__ ccell, T rc, T inv_h, T kc,
-                             uint16_t* __restrict__ lidx, T* __restrict__ sg, int64_t nslots)
+                             uint16_t* __restrict__ lidx, T* __restrict__ sg, int64_t nslots,
+                             const int* __restrict__ sell_ptr, const unsigned long long* __restrict__ sgq,
+                             const float* __restrict__ gunit)
 {
     __shared__ HaloRows h;
     const BrickInfo bi = info[blockIdx.x];
@@ -1079,7 +1255,14 @@ __global__ void k_bsell_fill(const BrickInfo* __restrict__ info, const int* __re
                 const int r = (cz - g.hz0) * h.hny + (cy - g.hy0);
                 l = h.hoff[r] + (j - h.hst[r]);
                 T gg[D];
-                PairG<T>::template g<D>(pi, ci, load_cpos<T>(cpos, j), ccell[j], rc, inv_h, kc, gg);
+                if (sgq) {
+                    // FP32 3D: the sliced-ELL layout's decoded value, bit for bit
+                    float x[3];
+                    gq_decode(sgq[(int64_t)sell_ptr[i >> 5] + t * 32 + (i & 31)], gunit[i], x);
+                    for (int q = 0; q < D; ++q) gg[q] = (T)x[q];
+                } else {
+                    PairG<T>::template g<D>(pi, ci, load_cpos<T>(cpos, j), ccell[j], rc, inv_h, kc, gg);
+                }
                 for (int q = 0; q < D; ++q) gq[q] = gg[q];
             }
             lidx[slot] = (uint16_t)l;
@@ -1168,12 +1351,12 @@ srdr_status build_bricks_typed(srdr_body* b)
         k_bsell_fill<T, 2><<<nbk, 128, 0, st>>>(b->binfo, b->cell_start, b->nc[0], b->nc[1], b->nc[2], d,
                                                 b->bown, b->bown_h, b->row_ptr, b->col, b->cell_of,
                                                 b->bsell_ptr, static_cast<const T*>(b->cpos), b->ccell, rcT,
-                                                ihT, kcT, b->blidx, sg, ns);
+                                                ihT, kcT, b->blidx, sg, ns, b->sell_ptr, b->sell_gq, b->gunit);
     else
         k_bsell_fill<T, 3><<<nbk, 128, 0, st>>>(b->binfo, b->cell_start, b->nc[0], b->nc[1], b->nc[2], d,
                                                 b->bown, b->bown_h, b->row_ptr, b->col, b->cell_of,
                                                 b->bsell_ptr, static_cast<const T*>(b->cpos), b->ccell, rcT,
-                                                ihT, kcT, b->blidx, sg, ns);
+                                                ihT, kcT, b->blidx, sg, ns, b->sell_ptr, b->sell_gq, b->gunit);
     SRDR_CK(cudaGetLastError());
     SRDR_TRY(dalloc(b, &b->ke_pp, b->n));
     SRDR_CK(cudaStreamSynchronize(st));
@@ -1216,6 +1399,26 @@ __global__ void k_sweep_consts(int n, T c, const T* __restrict__ mass, const T* 
     }
 }
 
+// slot records of the sweep: B = c w (one rounding, as the sweep would form
+// it) and the footprint-local index; the two spare records after the last
+// entry are zero (16-byte staging may read them)
+template <typename T>
+__global__ void k_sweep_slots(int64_t nnz, T c, const T* __restrict__ w, const uint16_t* __restrict__ loc,
+                              SweepSlot<T>* __restrict__ rec)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz + 2) return;
+    SweepSlot<T> r{};
+    if (k < nnz) {
+        if constexpr (sizeof(T) == 4)
+            r.B = __fmul_rn(c, w[k]);
+        else
+            r.B = __dmul_rn(c, w[k]);
+        r.loc = loc[k];
+    }
+    rec[k] = r;
+}
+
 template <typename T>
 srdr_status prepare_sweep_typed(srdr_body* b)
 {
@@ -1225,11 +1428,16 @@ srdr_status prepare_sweep_typed(srdr_body* b)
         SRDR_TRY(dalloc(b, &y, b->n));
         b->sbm = x;
         b->srd = y;
+        SweepSlot<T>* r = nullptr;
+        SRDR_TRY(dalloc(b, &r, (size_t)b->nnz + 2));
+        b->srec = r;
     }
     const T c = (T)(b->eta / b->desc.alpha * b->dt);
     k_sweep_consts<T><<<nblocks(b->n), kThreads, 0, b->stream>>>(
         (int)b->n, c, static_cast<const T*>(b->mass), static_cast<const T*>(b->sumw),
         static_cast<const T*>(b->sumw2), static_cast<T*>(b->sbm), static_cast<T*>(b->srd));
+    k_sweep_slots<T><<<nblocks(b->nnz + 2), kThreads, 0, b->stream>>>(
+        b->nnz, c, static_cast<const T*>(b->w), b->loc, static_cast<SweepSlot<T>*>(b->srec));
     SRDR_CK(cudaGetLastError());
     return SRDR_OK;
 }

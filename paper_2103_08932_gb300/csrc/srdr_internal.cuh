@@ -104,6 +104,49 @@ __device__ inline void lo_decode(const float (&h)[3], float packed, float (&l)[3
     }
 }
 
+// Packed pair gradient of the FP32 3D passes' stream: the three components
+// of g_ij as signed 21-bit multiples of the row's unit 2^(e_i - 20), where
+// |g_ij| < 2^e_i for every entry of row i.  One 8-byte stream word per slot
+// instead of three 4-byte components; each component is off by at most half
+// a unit (about 5e-7 of the row's largest component), and every decoded
+// value is an exact FP32 number, so G_i = sum_j g_ij summed from the decoded
+// values keeps the force sum's difference form exact.  The value 0 decodes
+// to g = 0 (padding slots).
+__device__ inline unsigned long long gq_encode(const float (&g)[3], float inv_unit)
+{
+    unsigned long long w = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        int q = __float2int_rn(g[c] * inv_unit);
+        q = q > 1048575 ? 1048575 : (q < -1048575 ? -1048575 : q);
+        w |= (unsigned long long)((unsigned)q & 0x1FFFFFu) << (21 * c);
+    }
+    return w;
+}
+__device__ inline void gq_decode(unsigned long long w, float unit, float (&g)[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int q = (int)((long long)(w << (43 - 21 * c)) >> 43);  // sign-extended field c
+        g[c] = __fmul_rn((float)q, unit);
+    }
+}
+
+// 1/2 m |v|^2 of one particle with explicit roundings: the same bits in
+// every kernel that evaluates it (no contraction choice left to the
+// compiler)
+template <typename T>
+__device__ inline double ke_particle(T m, const T (&v)[3])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float s = __fmaf_rn(v[2], v[2], __fmaf_rn(v[1], v[1], __fmul_rn(v[0], v[0])));
+        return (double)__fmul_rn(__fmul_rn(0.5f, m), s);
+    } else {
+        const double s = __fma_rn(v[2], v[2], __fma_rn(v[1], v[1], __dmul_rn(v[0], v[0])));
+        return __dmul_rn(__dmul_rn(0.5, m), s);
+    }
+}
+
 // grid-barrier buffer: kBarSub arrival sub-counters, a top counter and a
 // generation word, each on its own 128-byte line
 constexpr int kBarSub = 32;
@@ -127,6 +170,8 @@ struct StepArgs {
     const T* __restrict__ g0;   // [slots] V_j grad0_i W_ij, x component (sliced ELL)
     const T* __restrict__ g1;   // y component
     const T* __restrict__ g2;   // z component
+    const unsigned long long* __restrict__ gq;  // FP32 3D: [slots] packed g_ij (g0..g2 unused)
+    const float* __restrict__ gunit;            // FP32 3D: [n] unit of row i's packed components
     const T* __restrict__ cpos;   // [n][4] offset in its cell (x, y, z) and volume
     const int* __restrict__ ccell; // [n] packed cell coordinates x | y << 10 | z << 20
     const T* __restrict__ B0;   // [D*D][n]
@@ -149,6 +194,24 @@ struct StepArgs {
     T endl[3];
 };
 
+// One slot of a damping-sweep row: B_j = c w_ij, pre-scaled by the body's
+// c = eta~ dt (the same product the sweep would form, rounded once), and the
+// footprint-local index of j, so that the sweep reads a slot with one 8-byte
+// (FP32) or 16-byte (FP64) shared-memory load
+template <typename T>
+struct SweepSlot;
+template <>
+struct __align__(8) SweepSlot<float> {
+    float B;
+    unsigned loc;
+};
+template <>
+struct __align__(16) SweepSlot<double> {
+    double B;
+    unsigned loc;
+    unsigned pad;
+};
+
 template <typename T>
 struct SweepArgs {
     int n;
@@ -159,6 +222,7 @@ struct SweepArgs {
     const int* __restrict__ row_ptr;
     const uint16_t* __restrict__ loc;
     const T* __restrict__ w;
+    const SweepSlot<T>* __restrict__ rec;  // [nnz + 2] (B_j, footprint-local j) per row entry
     const T* __restrict__ mass;
     const T* __restrict__ sbm;   // [n] sum_j B_j - m_i of the local solve (Sec. 3.1)
     const T* __restrict__ srd;   // [n] 1 / ((sum_j B_j - m_i)^2 + sum_j B_j^2)
@@ -166,6 +230,12 @@ struct SweepArgs {
     DevScalars* sc;
     const int* dflag;  // device-decided damping of this step (graph replay), else null
     T c;          // 2 eta~ dt_loc, so that B_j = c w_ij
+    int cbase;    // colour base: 3 (3^d colours) or 2 (2^d colours over cells of edge 2 r_c)
+    int wrad;     // cells within wrad on every axis may touch common particles (2, or 1)
+    const int* __restrict__ foot_ptr;  // 2^d layout: touched lists per cell, else null
+    const int* __restrict__ foot_tab;
+    const int* __restrict__ own_off;
+    int rows_global;  // 1: the cells' slot records are read from global memory, not staged
     int pairwise;
     int max_foot;
     int max_pairs;
@@ -184,6 +254,15 @@ struct srdr_body {
     int ncells = 0, ncells_nonempty = 0, ncolours = 0;
     cudaStream_t stream = nullptr;
     double h = 0, rc = 0, lambda = 0, mu = 0, eta = 0, dt = 0, vol0 = 0;
+    double cut = 0;   // neighbour cut-off 2h (rc is the cell edge: cut, or 2 cut in the 2^d layout)
+    int cbase = 3;    // colour base of the sweep layout: 3 (3^d colours) or 2 (2^d colours)
+    // 2^d layout: the particles each cell's sweep touches (its own and their
+    // neighbours, ascending sorted index), foot_tab[foot_ptr[c] ..
+    // foot_ptr[c+1]-1], and the position of the cell's first particle in it;
+    // null in the paper's layout, whose footprint is the 3^d neighbour cells
+    int* foot_ptr = nullptr;
+    int* foot_tab = nullptr;
+    int* own_off = nullptr;
     double lo[3] = {0, 0, 0};
 
     // device arrays
@@ -205,7 +284,9 @@ struct srdr_body {
     int64_t nslots = 0;
     int* sell_ptr = nullptr;
     int* sell_col = nullptr;
-    void* sell_g = nullptr;     // T [3][slots] pair gradients in sliced-ELL order
+    void* sell_g = nullptr;     // T [3][slots] pair gradients in sliced-ELL order (FP64, 2D)
+    unsigned long long* sell_gq = nullptr;  // FP32 3D: [slots] packed pair gradients
+    float* gunit = nullptr;     // FP32 3D: [n] unit of each row's packed components
     void* cpos = nullptr;       // T [n][4] offset in its cell and volume
     int* ccell = nullptr;       // [n] packed cell coordinates
     void* B0 = nullptr;         // T [D*D][n]
@@ -213,6 +294,7 @@ struct srdr_body {
     void* Gs = nullptr;         // T [3][n]
     void* sumw = nullptr;
     void* sumw2 = nullptr;
+    void* srec = nullptr;        // SweepSlot<T> [nnz + 2] pre-scaled sweep slots (prepare_sweep)
     void* sbm = nullptr;         // T [n] per-particle constants of the local solve
     void* srd = nullptr;         //   (prepare_sweep; B_j = c w_ij with the body's c)
     void* v = nullptr;          // T [n][4] (vx, vy, vz, 1/m)
@@ -249,6 +331,7 @@ struct srdr_body {
     int sweep_warps_per_block = 1;   // warps per block of the sweep kernel (1, 4)
     int sweep_tuned = 0;
     int sweep_smem = 0;
+    int sweep_rows_global = 0;       // slot records read from global memory (staging does not fit)
     int sweep_sync = SRDR_SWEEP_AUTO;  // requested synchronisation of the sweep's colour phases
     int sweep_cellwise = 1;            // the one in use: cell-wise waits (1) or grid barriers (0)
     unsigned* flow = nullptr;          // cell-wise synchronisation words (k_sweep_flow)
@@ -328,7 +411,8 @@ srdr_status build_body(srdr_body* b, int64_t n, const double* r0, const double* 
                        const uint8_t* flags, const double* u0);
 // per-particle constants of the damping sweep's local solve for the body's
 // current eta~ and dt (setup.cu): sbm = c sum_j w_ij - m_i and
-// srd = 1 / (sbm^2 + c^2 sum_j w_ij^2) with c = 2 eta~ dt_loc
+// srd = 1 / (sbm^2 + c^2 sum_j w_ij^2) with c = 2 eta~ dt_loc; and the
+// sweep's slot records (B_j = c w_ij, footprint-local j)
 srdr_status prepare_sweep(srdr_body* b);
 // brick layout of the tiled passes (setup.cu): builds it for the requested
 // brick size; b->bricks_built = 1 when built, -1 when a halo does not fit
@@ -342,6 +426,8 @@ void prof_begin(srdr_body* b, int k, cudaEvent_t* ev);
 void prof_end(srdr_body* b, int k, cudaEvent_t ev);
 // stepping (step.cu)
 srdr_status launch_steps(srdr_body* b, int64_t nsteps);
+// zero the damping sweep's synchronisation words after a wait ran out (api.cu)
+srdr_status reset_sync_words(srdr_body* b);
 srdr_status sync_scalars(const srdr_body* b);
 srdr_status reset_scalars(srdr_body* b, double tol);
 

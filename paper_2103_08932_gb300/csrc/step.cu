@@ -47,6 +47,14 @@ __global__ void k_set_tol(DevScalars* sc, double tol)
     if (sc->status == DEV_OK) sc->done = 0;
 }
 
+// clears a DEV_TIMEOUT left by an autotuner's timing launch (on a scratch
+// copy of v: the state is untouched); reports it in *out
+__global__ void k_take_timeout(DevScalars* sc, int* out)
+{
+    *out = sc->status == DEV_TIMEOUT;
+    if (sc->status == DEV_TIMEOUT) sc->status = DEV_OK;
+}
+
 // ------------------------------------------------------------------ host side
 
 template <typename T>
@@ -63,6 +71,7 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     s.row_ptr = b->row_ptr;
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
+    s.rec = static_cast<const SweepSlot<T>*>(b->srec);
     s.mass = static_cast<const T*>(b->mass);
     s.sbm = static_cast<const T*>(b->sbm);
     s.srd = static_cast<const T*>(b->srd);
@@ -71,8 +80,14 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     // B_j = 2 eta~ V_i V_j W'/r dt_loc with eta~ = eta / alpha, dt_loc = dt / 2
     s.c = (T)(b->eta / b->desc.alpha * b->dt);
     s.pairwise = b->desc.damping == SRDR_DAMP_PAIRWISE;
+    s.cbase = b->cbase;
+    s.wrad = b->cbase == 3 ? 2 : 1;
+    s.foot_ptr = b->foot_ptr;
+    s.foot_tab = b->foot_tab;
+    s.own_off = b->own_off;
     s.max_foot = b->max_foot;
-    s.max_pairs = b->max_pairs;
+    s.rows_global = b->sweep_rows_global;
+    s.max_pairs = b->sweep_rows_global ? 0 : b->max_pairs;  // no staged rows then
     s.max_cell = b->max_cell;
     return s;
 }
@@ -93,7 +108,14 @@ struct SweepLaunch {
 template <typename T, int D, int G, int W>
 srdr_status sweep_launch_gw(srdr_body* b, SweepLaunch<T, D>* out)
 {
-    const size_t smem = (size_t)G * W * cell_smem_bytes<T, D>(b->max_foot, b->max_pairs, b->max_cell);
+    // the rows are staged in shared memory when a cell's fit, else read
+    // through the caches (large cells of the 2^d layout)
+    size_t smem = (size_t)G * W * cell_smem_bytes<T, D>(b->max_foot, b->max_pairs, b->max_cell);
+    b->sweep_rows_global = 0;
+    if (smem > 227 * 1024 && b->cbase == 2) {
+        smem = (size_t)G * W * cell_smem_bytes<T, D>(b->max_foot, 0, b->max_cell);
+        b->sweep_rows_global = 1;
+    }
     if (smem > 227 * 1024) {
         set_error("damping sweep needs %zu bytes of shared memory per block (limit 227 KB)", smem);
         return SRDR_ERR_INVALID;
@@ -149,6 +171,8 @@ srdr_status autotune_sweep(srdr_body* b)
     b->sweep_tuned = 1;
     T* vtmp = nullptr;
     SRDR_TRY(dalloc(b, &vtmp, (size_t)4 * b->n));
+    int* tflag = nullptr;
+    SRDR_TRY(dalloc(b, &tflag, 1));
     SRDR_CK(cudaMemcpyAsync(vtmp, b->v, sizeof(T) * 4 * (size_t)b->n, cudaMemcpyDeviceToDevice,
                             b->stream));
     SweepArgs<T> sw = make_sweep_args<T>(b);
@@ -175,6 +199,8 @@ srdr_status autotune_sweep(srdr_body* b)
             b->sweep_warps_per_block = w;
             SweepLaunch<T, D> sl;
             if (sweep_launch<T, D>(b, &sl) != SRDR_OK) continue;  // e.g. too much shared memory
+            sw.rows_global = b->sweep_rows_global;  // the staging this mapping can afford
+            sw.max_pairs = b->sweep_rows_global ? 0 : b->max_pairs;
             sync = sl.sync;
             SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params, sl.smem,
                                                 b->stream));
@@ -182,7 +208,17 @@ srdr_status autotune_sweep(srdr_body* b)
             SRDR_CK(cudaLaunchCooperativeKernel(sl.fn, dim3(sl.grid), dim3(sl.threads), params, sl.smem,
                                                 b->stream));
             SRDR_CK(cudaEventRecord(e1, b->stream));
+            k_take_timeout<<<1, 1, 0, b->stream>>>(b->sc, tflag);
+            int ran_out = 0;
+            SRDR_CK(cudaMemcpyAsync(&ran_out, tflag, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
             SRDR_CK(cudaEventSynchronize(e1));
+            SRDR_CK(cudaStreamSynchronize(b->stream));
+            if (ran_out) {
+                // a wait of this mapping ran out: its words are mid-sweep and
+                // the mapping is not a candidate
+                SRDR_TRY(reset_sync_words(b));
+                continue;
+            }
             float ms = 0.f;
             SRDR_CK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) {
@@ -197,6 +233,7 @@ srdr_status autotune_sweep(srdr_body* b)
     b->sweep_cellwise = best_c;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    SRDR_TRY(dev_free(b, tflag));
     return dev_free(b, vtmp);
 }
 
@@ -236,16 +273,16 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
                          b->desc.alpha > 0.0 && b->eta > 0.0;
     const T c2eta_dt = (T)(2.0 * b->eta * b->dt);
     if (damping && !b->sbm) SRDR_TRY(prepare_sweep(b));
-    SweepArgs<T> sw = make_sweep_args<T>(b);
     SweepLaunch<T, D> sl;
     if (damping && !b->sweep_tuned) SRDR_TRY((autotune_sweep<T, D>(b)));
     if (damping) SRDR_TRY((sweep_launch<T, D>(b, &sl)));
+    SweepArgs<T> sw = make_sweep_args<T>(b);  // after sweep_launch chose the staging
     const size_t smem = sl.smem;
     const int grid = sl.grid;
     const int* cptr = b->colour_ptr_d;
     int ncol = b->ncolours;
     unsigned* bar = damping ? sl.sync : b->bar;  // grid barrier or cell-wise words
-    if (damping && (!sw.colour_cells || !sw.cell_start || !sw.row_ptr || !sw.loc || !sw.w ||
+    if (damping && (!sw.colour_cells || !sw.cell_start || !sw.row_ptr || !sw.loc || !sw.w || !sw.rec ||
                     !sw.mass || !sw.sbm || !sw.srd || !sw.v || !cptr || !bar)) {
         set_error("damping sweep tables are not built");
         return SRDR_ERR_INVALID;

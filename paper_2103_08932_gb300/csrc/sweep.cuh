@@ -112,7 +112,7 @@ __device__ inline FootRuns foot_runs_group(int c, int dim, int nx, int ny, int n
 // arrival of a sub-counter resets it and arrives at the top counter; the last
 // arrival there resets it and bumps the generation.  Waiters poll the
 // generation (its own line, so polling does not slow the counters) with a
-// sleep and give up after one second, setting DEV_TIMEOUT in sc->status, so
+// sleep and give up after five seconds, setting DEV_TIMEOUT in sc->status, so
 // the host gets an error instead of a hung GPU.  Between arrive and wait a
 // block may do work that does not depend on other blocks.
 __device__ inline unsigned bar_arrive(unsigned* bar, unsigned nblocks)
@@ -144,10 +144,13 @@ __device__ inline unsigned long long global_ns()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bound of every wait of the sweep: far above one colour phase of any body
-// that fits on the device, short enough for a test to run one out
-constexpr unsigned long long kWaitNs = 1000000000ull;
-constexpr long long kWaitPolls = 1LL << 24;
+// bound of every wait of the sweep: far above the sweep of any body that
+// fits on the device (a cell-wise wait may span all earlier colour phases:
+// about 0.6 s for FP64 pairwise updates of the 2^d layout's large cells),
+// short enough for a test to run one out; the poll count bounds the wait
+// too, set above what the time bound allows
+constexpr unsigned long long kWaitNs = 5000000000ull;
+constexpr long long kWaitPolls = 1LL << 27;
 
 __device__ inline bool bar_wait(unsigned* bar, unsigned g, DevScalars* sc)
 {
@@ -172,63 +175,59 @@ __device__ inline bool bar_wait(unsigned* bar, unsigned g, DevScalars* sc)
 // Per cell (group), each section on a 16-byte boundary:
 //   sv [F + 1] footprint velocity records (vx, vy, vz, 1/m) and a zero
 //   record at F that padded neighbour slots point at,
-//   sw [P + 2E] CSR weights, copied in 16-byte chunks from the chunk holding
-//   the cell's first row entry (E = 16 / sizeof(T) entries per chunk),
+//   srec [P + 2] the rows' slot records (B_j pre-scaled, footprint-local j),
+//   copied in 16-byte chunks from the chunk holding the cell's first row
+//   entry (R = 16 / sizeof(SweepSlot<T>) records per chunk),
 //   sm / sbm / srd [C] per particle of the cell: mass, sum_B - m_i and
 //   1 / ((sum_B - m_i)^2 + sum_B^2) (precomputed per body),
 //   srow [C+1] absolute row starts,
-//   sl [P + 16] footprint-local indices (uint16), 16-byte chunks like sw,
 //   sfoot [F] the sorted particle index of each footprint-local index.
 template <typename T, int D>
 struct CellSmem {
     vec4_t<T>* sv;
-    T* sw;
+    SweepSlot<T>* srec;
     T* sm;
     T* sbm;
     T* srd;
     int* srow;
-    uint16_t* sl;
     int* sfoot;
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// byte offsets of the sections after sv: sw, sm (then sbm, srd), srow, sl,
+// byte offsets of the sections after sv: srec, sm (then sbm, srd), srow,
 // sfoot, end
 template <typename T, int D>
-__host__ __device__ inline void cell_smem_offsets(int F, int P, int C, size_t (&o)[6])
+__host__ __device__ inline void cell_smem_offsets(int F, int P, int C, size_t (&o)[5])
 {
-    constexpr int E = 16 / (int)sizeof(T);
     o[0] = align16(sizeof(T) * 4 * ((size_t)F + 1));
-    o[1] = o[0] + align16(sizeof(T) * ((size_t)P + 2 * E));
+    o[1] = o[0] + align16(sizeof(SweepSlot<T>) * ((size_t)P + 2));
     o[2] = o[1] + align16(sizeof(T) * 3 * (size_t)C);
     o[3] = o[2] + align16(sizeof(int) * ((size_t)C + 1));
-    o[4] = o[3] + align16(sizeof(uint16_t) * ((size_t)P + 16));
-    o[5] = o[4] + align16(sizeof(int) * (size_t)F);
+    o[4] = o[3] + align16(sizeof(int) * (size_t)F);
 }
 
 template <typename T, int D>
 __host__ __device__ inline size_t cell_smem_bytes(int F, int P, int C)
 {
-    size_t o[6];
+    size_t o[5];
     cell_smem_offsets<T, D>(F, P, C, o);
-    return o[5];
+    return o[4];
 }
 
 template <typename T, int D>
 __device__ inline CellSmem<T, D> cell_smem(unsigned char* raw, int F, int P, int C)
 {
-    size_t o[6];
+    size_t o[5];
     cell_smem_offsets<T, D>(F, P, C, o);
     CellSmem<T, D> s;
     s.sv = reinterpret_cast<vec4_t<T>*>(raw);
-    s.sw = reinterpret_cast<T*>(raw + o[0]);
+    s.srec = reinterpret_cast<SweepSlot<T>*>(raw + o[0]);
     s.sm = reinterpret_cast<T*>(raw + o[1]);
     s.sbm = s.sm + C;
     s.srd = s.sbm + C;
     s.srow = reinterpret_cast<int*>(raw + o[2]);
-    s.sl = reinterpret_cast<uint16_t*>(raw + o[3]);
-    s.sfoot = reinterpret_cast<int*>(raw + o[4]);
+    s.sfoot = reinterpret_cast<int*>(raw + o[3]);
     return s;
 }
 
@@ -259,26 +258,33 @@ __device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellS
     st.cs = __ldg(a.cell_start + c);
     const int ce = __ldg(a.cell_start + c + 1);
     st.np = ce - st.cs;
-    st.fr = foot_runs_group<L>(c, a.dim, a.nx, a.ny, a.nz, a.cell_start, gl, gmask);
-    st.my_off = 0;
+    if (a.foot_tab) {
+        // 2^d layout: the cell's touched particles, listed at set-up
+        const int f0 = __ldg(a.foot_ptr + c);
+        st.fr.nruns = 0;
+        st.fr.total = __ldg(a.foot_ptr + c + 1) - f0;
+        st.my_off = __ldg(a.own_off + c);
+        for (int q = gl; q < st.fr.total; q += L) cp_async4(s.sfoot + q, a.foot_tab + f0 + q);
+    } else {
+        st.fr = foot_runs_group<L>(c, a.dim, a.nx, a.ny, a.nz, a.cell_start, gl, gmask);
+        st.my_off = 0;
 #pragma unroll
-    for (int r = 0; r < 9; ++r)
-        if (r < st.fr.nruns && st.cs >= st.fr.a[r] && st.cs < st.fr.a[r] + (st.fr.off[r + 1] - st.fr.off[r]))
-            st.my_off = st.fr.off[r] + (st.cs - st.fr.a[r]);
+        for (int r = 0; r < 9; ++r)
+            if (r < st.fr.nruns && st.cs >= st.fr.a[r] && st.cs < st.fr.a[r] + (st.fr.off[r + 1] - st.fr.off[r]))
+                st.my_off = st.fr.off[r] + (st.cs - st.fr.a[r]);
+    }
     st.p0 = __ldg(a.row_ptr + st.cs);
     st.p1 = __ldg(a.row_ptr + ce);
     const int p0 = st.p0, p1 = st.p1, np = st.np;
-    {
-        // weights and footprint-local indices in 16-byte chunks from the
-        // chunk holding entry p0 (the arrays are allocated with a spare
-        // chunk, so the last chunk stays inside them)
-        constexpr int E = 16 / (int)sizeof(T);
-        const int wb = p0 & ~(E - 1);
-        for (int k = wb + gl * E; k < p1; k += L * E) cp_async16s(s.sw + (k - wb), a.w + k);
-        const int lb = p0 & ~7;
-        for (int k = lb + gl * 8; k < p1; k += L * 8) cp_async16s(s.sl + (k - lb), a.loc + k);
+    if (!a.rows_global) {
+        // slot records in 16-byte chunks from the chunk holding entry p0
+        // (the array has two spare records, so the last chunk stays inside it)
+        constexpr int R = 16 / (int)sizeof(SweepSlot<T>);
+        const int rb = p0 & ~(R - 1);
+        for (int k = rb + gl * R; k < p1; k += L * R) cp_async16s(s.srec + (k - rb), a.rec + k);
     }
-    // footprint-local index -> sorted particle index
+    // footprint-local index -> sorted particle index (the 3^d neighbour
+    // cells' runs; the 2^d layout's list is being copied above)
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         if (r < st.fr.nruns) {
@@ -308,9 +314,12 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
     const int np = st.np, p0 = st.p0, my_off = st.my_off;
     const int Ftot = st.fr.total;
     V4* sv = s.sv;
-    const T* sw = s.sw + (p0 & (16 / (int)sizeof(T) - 1));  // entry k at sw[k - p0]
+    // entry k of the cell's rows at rec[k - p0]: staged in shared memory, or
+    // (cells whose rows do not fit) read through the caches
+    const SweepSlot<T>* rec =
+        a.rows_global ? a.rec + p0 : s.srec + (p0 & (16 / (int)sizeof(SweepSlot<T>) - 1));
     const int* sfoot = s.sfoot;
-    const T cc = a.c;
+    if (a.foot_tab) cp_async_wait_all();  // the touched list arrives by cp.async
     __syncwarp(gmask);  // the footprint table written by other lanes of the group
 
     // velocity records from L2 straight into shared memory
@@ -326,7 +335,6 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
     if (gl == 0) sv[a.max_foot] = V4{T(0), T(0), T(0), T(0)};
     cp_async_wait_all();
     __syncwarp(gmask);
-    const uint16_t* sl = s.sl + (p0 & 7);  // entry k at sl[k - p0]
     const int pad = a.max_foot;  // the zero record: padded slots read and write it with B = 0
 
     for (int dir = mode == 1 ? 1 : 0; dir <= (mode == 0 ? 0 : 1); ++dir) {
@@ -351,9 +359,13 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
 #pragma unroll
             for (int m = 0; m < NK; ++m) {
                 const int k = a0 + gl + m * L;
-                const bool ok = k < a1;
-                j_[m] = ok ? (int)sl[k] : pad;
-                b_[m] = ok ? cc * sw[k] : T(0);
+                j_[m] = pad;
+                b_[m] = T(0);
+                if (k < a1) {
+                    const SweepSlot<T> r = rec[k];
+                    j_[m] = (int)r.loc;
+                    b_[m] = r.B;
+                }
             }
         };
         if (np > 0) slots(0, jj, BB, k0, k1);
@@ -398,9 +410,10 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
                     for (int w = 0; w < V; ++w) {
                         const int k = kb + w * L;
                         if (k < k1) {
-                            const V4 x = sv[sl[k]];
+                            const SweepSlot<T> r = rec[k];
+                            const V4 x = sv[r.loc];
                             const T xd[3] = {x.x, x.y, x.z};
-                            const T B = cc * sw[k];
+                            const T B = r.B;
 #pragma unroll
                             for (int d = 0; d < D; ++d) acc[w][d] -= B * (vi[d] - xd[d]);
                         }
@@ -440,8 +453,9 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
                 }
             } else {
                 for (int k = k0 + gl; k < k1; k += L) {
-                    const int j = sl[k];
-                    const T B = cc * sw[k];
+                    const SweepSlot<T> r = rec[k];
+                    const int j = (int)r.loc;
+                    const T B = r.B;
                     const V4 x = sv[j];
                     const T xd[3] = {x.x, x.y, x.z};
                     T o[3] = {xd[0], xd[1], xd[2]};
@@ -472,12 +486,13 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
                 const int li = my_off + p;
                 const int k0 = s.srow[p] - p0, k1 = s.srow[p + 1] - p0;
                 const T mi = s.sm[p];
-                const T ch = T(0.5) * cc;
                 for (int pass = 0; pass < 2; ++pass) {
                     for (int t2 = 0; t2 < k1 - k0; ++t2) {
                         const int k = pass == 0 ? k0 + t2 : k1 - 1 - t2;
-                        const int j = sl[k];
-                        const T B = ch * sw[k];
+                        const SweepSlot<T> r = rec[k];
+                        const int j = (int)r.loc;
+                        // half the step: (c/2) w = B/2 exactly (a power-of-two scaling)
+                        const T B = T(0.5) * r.B;
                         V4 xi = sv[li], xj = sv[j];
                         const T mj = T(1) / xj.w;
                         const T den = mi * mj - (mi + mj) * B;
@@ -643,15 +658,19 @@ __device__ inline bool flow_wait(const SweepArgs<T>& a, const unsigned* done, un
 {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-    const int nb = a.dim == 3 ? 125 : 25;
+    // cells within wrad on every axis: 2 for cells of edge r_c (3^d
+    // footprints overlap up to 2 cells apart), 1 for cells of edge 2 r_c
+    // (what they touch lies within r_c of them)
+    const int wr = a.wrad, ww = 2 * wr + 1, q = a.cbase;
+    const int nb = a.dim == 3 ? ww * ww * ww : ww * ww;
     bool ok = true;
     for (int o = gl; o < nb && ok; o += L) {
-        const int dx = o % 5 - 2, dy = (o / 5) % 5 - 2, dz = a.dim == 3 ? o / 25 - 2 : 0;
+        const int dx = o % ww - wr, dy = (o / ww) % ww - wr, dz = a.dim == 3 ? o / (ww * ww) - wr : 0;
         const int x = cx + dx, y = cy + dy, z = cz + dz;
         if ((dx | dy | dz) == 0 || x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) continue;
         const int d = x + nx * (y + ny * z);
         if (__ldg(a.cell_start + d + 1) == __ldg(a.cell_start + d)) continue;  // empty: never runs
-        const int col = x % 3 + 3 * (y % 3) + 9 * (z % 3);
+        const int col = x % q + q * (y % q) + q * q * (z % q);
         const unsigned need = 2u * epoch + phases_before(col, ph, ncolours, clast);
         long long polls = 0;
         unsigned long long t0 = 0;

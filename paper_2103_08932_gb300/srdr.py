@@ -38,6 +38,8 @@ SRDR_LINEAR_SVK, SRDR_NEO_HOOKEAN = 0, 1
 SRDR_FP64, SRDR_FP32_MIXED = 0, 1
 SRDR_DAMP_NONE, SRDR_DAMP_PARTICLE, SRDR_DAMP_PAIRWISE, SRDR_DAMP_EXPLICIT = 0, 1, 2, 3
 SRDR_FLAG_CONSTRAINED, SRDR_FLAG_END_LOAD = 1, 2
+SRDR_SWEEP_LAYOUT_3D, SRDR_SWEEP_LAYOUT_2D = 0, 1
+SRDR_BATCH_AUTO, SRDR_BATCH_SHARED, SRDR_BATCH_STREAMS = 0, 1, 2
 SRDR_FIELD_PB, SRDR_FIELD_B0 = 0, 1
 
 # every symbol include/srdr.h declares
@@ -49,7 +51,7 @@ EXPORTS = [
     "srdr_random_phi", "srdr_body_profile", "srdr_body_kernel_times",
     "srdr_kinetic_energy_noalloc", "srdr_body_tune", "srdr_desc_particle_count",
     "srdr_body_pass_mapping", "srdr_body_sweep_sync", "srdr_body_debug_stall_sweep",
-    "srdr_batch_create", "srdr_batch_step", "srdr_batch_run", "srdr_batch_info",
+    "srdr_batch_create", "srdr_batch_step", "srdr_batch_run", "srdr_batch_info", "srdr_batch_mode",
     "srdr_batch_destroy", "srdr_batch_relax", "srdr_server_create", "srdr_server_configure",
     "srdr_server_submit", "srdr_server_poll", "srdr_server_wait", "srdr_server_stats",
     "srdr_server_destroy",
@@ -84,6 +86,7 @@ class srdr_body_desc(C.Structure):
         ("precision", C.c_int),
         ("dt", C.c_double),
         ("twist", C.c_double * 4),
+        ("sweep_layout", C.c_int),
     ]
 
 
@@ -145,6 +148,7 @@ def lib():
         "srdr_batch_info": (st, [p, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_int),
                                  C.POINTER(C.c_int)]),
         "srdr_batch_destroy": (None, [p]),
+        "srdr_batch_mode": (st, [p, C.c_int]),
         "srdr_batch_relax": (st, [p, C.c_int, d, i64, p, p]),
     }
     for name, (rt, args) in sig.items():
@@ -169,7 +173,8 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
-def make_desc(spec, precision=SRDR_FP64, damping=SRDR_DAMP_PARTICLE, dt=0.0) -> srdr_body_desc:
+def make_desc(spec, precision=SRDR_FP64, damping=SRDR_DAMP_PARTICLE, dt=0.0,
+              sweep_layout=0) -> srdr_body_desc:
     """C description from a synth.BodySpec-like object."""
     d = srdr_body_desc()
     d.dim = spec.dim
@@ -192,6 +197,7 @@ def make_desc(spec, precision=SRDR_FP64, damping=SRDR_DAMP_PARTICLE, dt=0.0) -> 
     d.precision = precision
     d.dt = dt
     d.twist = (C.c_double * 4)(*getattr(spec, "twist", (0.0, 0.0, 0.0, 0.0)))
+    d.sweep_layout = sweep_layout
     return d
 
 
@@ -359,6 +365,10 @@ class Batch:
 
     def step(self, nsteps=1):
         _check(lib().srdr_batch_step(self.h, int(nsteps)))
+
+    def mode(self, mode=SRDR_BATCH_AUTO):
+        """SRDR_BATCH_AUTO (0), SRDR_BATCH_SHARED (1) or SRDR_BATCH_STREAMS (2)."""
+        _check(lib().srdr_batch_mode(self.h, int(mode)))
 
     def run(self, ke_ratio=1e-8, max_steps=10**6):
         nb = len(self.bodies)

@@ -73,6 +73,7 @@ def test_entry_points_reject_null_handles_without_gpu(L):
         lambda: L.srdr_body_stats(None, None),
         lambda: L.srdr_batch_step(None, 1),
         lambda: L.srdr_batch_info(None, None, None, None, None),
+        lambda: L.srdr_batch_mode(None, srdr.SRDR_BATCH_STREAMS),
     ]
     for call in calls:
         assert call() == srdr.SRDR_ERR_INVALID

@@ -42,14 +42,19 @@ def uneven_specs(dim=3):
     ]
 
 
+MODES = [srdr.SRDR_BATCH_SHARED, srdr.SRDR_BATCH_STREAMS]
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["shared", "streams"])
 @pytest.mark.parametrize("dim,precision,sync", [
     (3, srdr.SRDR_FP64, srdr.SRDR_SWEEP_AUTO), (3, srdr.SRDR_FP32_MIXED, srdr.SRDR_SWEEP_AUTO),
     (2, srdr.SRDR_FP64, srdr.SRDR_SWEEP_AUTO), (3, srdr.SRDR_FP32_MIXED, srdr.SRDR_SWEEP_CELLS),
     (3, srdr.SRDR_FP64, srdr.SRDR_SWEEP_BARRIER), (2, srdr.SRDR_FP32_MIXED, srdr.SRDR_SWEEP_CELLS)])
-def test_batch_steps_equal_single_bodies(dim, precision, sync):
-    """Batched steps (barrier or cell-wise batched sweep) equal the same
-    bodies stepped alone (cell-wise or barrier single-body sweep) bit for bit;
-    the bodies then keep stepping alone and still agree."""
+def test_batch_steps_equal_single_bodies(dim, precision, sync, mode):
+    """Batched steps (shared launches with a barrier or cell-wise batched
+    sweep, or every body on its own stream) equal the same bodies stepped
+    alone (cell-wise or barrier single-body sweep) bit for bit; the bodies
+    then keep stepping alone and still agree."""
     specs = uneven_specs(dim)
     single = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
     for b in single:
@@ -59,6 +64,7 @@ def test_batch_steps_equal_single_bodies(dim, precision, sync):
     for b in bodies:
         b.sweep_sync(sync)
     batch = srdr.Batch(bodies)
+    batch.mode(mode)
     batch.step(40)
     info = batch.info()
     assert info["sweep_cells_per_warp"] in (1, 2, 4) and info["pass_threads"] in (128, 256, 512)
@@ -74,7 +80,8 @@ def test_batch_steps_equal_single_bodies(dim, precision, sync):
         assert sa["ke"] == sb["ke"]
 
 
-def test_batch_relax_retires_each_body_at_its_own_step():
+@pytest.mark.parametrize("mode", MODES, ids=["shared", "streams"])
+def test_batch_relax_retires_each_body_at_its_own_step(mode):
     specs = uneven_specs(3)
     tol = 1e-6
     single_steps, single_u = [], []
@@ -85,6 +92,7 @@ def test_batch_relax_retires_each_body_at_its_own_step():
         single_u.append(b.displacement())
     bodies = [srdr.Body(srdr.make_desc(s)) for s in specs]
     batch = srdr.Batch(bodies)
+    batch.mode(mode)
     status, st, steps = batch.run(tol, 200000)
     assert status == srdr.SRDR_OK and list(st) == [0] * len(specs)
     assert list(steps) == single_steps
@@ -106,10 +114,12 @@ def test_batch_relax_one_call():
         assert np.array_equal(b.displacement(), u)
 
 
-def test_batch_step_cap_reports_not_converged():
+@pytest.mark.parametrize("mode", MODES, ids=["shared", "streams"])
+def test_batch_step_cap_reports_not_converged(mode):
     specs = uneven_specs(3)[:1]
     bodies = [srdr.Body(srdr.make_desc(s)) for s in specs]
     batch = srdr.Batch(bodies)
+    batch.mode(mode)
     status, st, steps = batch.run(1e-12, 50)
     assert status == srdr.SRDR_ERR_NOT_CONVERGED
     assert list(st) == [srdr.SRDR_ERR_NOT_CONVERGED] and list(steps) == [50]
@@ -161,3 +171,11 @@ def test_batched_bodies_at_convergence_match_oracle(precision):
             assert err <= 1e-9
             assert b.stats()["damped_steps"] == damped
     batch.close()
+
+
+def test_batch_mode_rejects_unknown():
+    b = srdr.Body(srdr.make_desc(uneven_specs(3)[0]))
+    batch = srdr.Batch([b])
+    with pytest.raises(srdr.SrdrError) as e:
+        batch.mode(5)
+    assert e.value.status == srdr.SRDR_ERR_INVALID

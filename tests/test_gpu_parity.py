@@ -381,7 +381,7 @@ def test_sweep_sync_modes_are_bitwise_equal(spec, precision, damping, jit):
 def test_sweep_wait_that_runs_out_is_reported(mode):
     """Failure path of the sweep's bounded waits: a test hook sets the
     synchronisation words to counts no cell reaches, every wait of the next
-    sweep gives up after its bound (about a second), relax returns
+    sweep gives up after its bound (about five seconds), relax returns
     SRDR_ERR_TIMEOUT, and the body stays usable: after restoring a state it
     steps exactly like an untouched body from that state."""
     ref = gpu_for(SMALL3D, precision=srdr.SRDR_FP64)
