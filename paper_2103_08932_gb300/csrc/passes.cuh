@@ -27,32 +27,6 @@ __device__ inline uint16_t ld_stream(const uint16_t* p)
     asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(r) : "l"(p));
     return r;
 }
-__device__ inline unsigned long long ld_stream(const unsigned long long* p)
-{
-    unsigned long long r;
-    asm volatile("ld.global.nc.L1::no_allocate.b64 %0, [%1];" : "=l"(r) : "l"(p));
-    return r;
-}
-
-// the FP32 3D passes stream packed pair gradients (gq_encode)
-template <typename T, int D>
-constexpr bool kPackedG = sizeof(T) == 4 && D == 3;
-
-// slot k's pair gradient: packed (FP32 3D, unit of the row) or three streams
-template <typename T, int D>
-__device__ inline void load_g(const StepArgs<T>& a, int k, bool in, float unit, T (&g)[D])
-{
-    if constexpr (kPackedG<T, D>) {
-        float x[3];
-        gq_decode(in ? ld_stream(a.gq + k) : 0ull, unit, x);
-#pragma unroll
-        for (int q = 0; q < D; ++q) g[q] = x[q];
-    } else {
-        g[0] = in ? ld_stream(a.g0 + k) : T(0);
-        g[1] = in ? ld_stream(a.g1 + k) : T(0);
-        if constexpr (D == 3) g[2] = in ? ld_stream(a.g2 + k) : T(0);
-    }
-}
 
 // ------------------------------------------------------------------ layouts
 // u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 records [n][4]
@@ -318,7 +292,6 @@ __device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
     int width = (__ldg(a.sell_ptr + s + 1) - base) >> 5;
     T xi[3], li[3];
     UAcc<T>::load(a.u, a.uhi, a.ulo, i, xi, li);
-    const float unit = kPackedG<T, D> ? __ldg(a.gunit + i) : 0.f;
     T G[D][D];
 #pragma unroll
     for (int p = 0; p < D; ++p)
@@ -335,7 +308,9 @@ __device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
             const int k = base + (t0 + u) * 32 + lane;
             const bool in = t0 + u < width;
             jj[u] = in ? ld_stream(a.sell_col + k) : i;
-            load_g<T, D>(a, k, in, unit, gg[u]);
+            gg[u][0] = in ? ld_stream(a.g0 + k) : T(0);
+            gg[u][1] = in ? ld_stream(a.g1 + k) : T(0);
+            if constexpr (D == 3) gg[u][2] = in ? ld_stream(a.g2 + k) : T(0);
         }
         T xj[kUnroll][3], lj[kUnroll][3];
 #pragma unroll
@@ -594,7 +569,6 @@ __device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_
     int width = (__ldg(a.sell_ptr + s + 1) - base) >> 5;
     T Pi[D][D];
     PBL<T, D>::load(a.PB, a.n, i, Pi);
-    const float unit = kPackedG<T, D> ? __ldg(a.gunit + i) : 0.f;
     T acc[D];
 #pragma unroll
     for (int p = 0; p < D; ++p) acc[p] = 0;
@@ -606,7 +580,9 @@ __device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_
             const int k = base + (t0 + u) * 32 + lane;
             const bool in = t0 + u < width;
             jj[u] = in ? ld_stream(a.sell_col + k) : i;
-            load_g<T, D>(a, k, in, unit, gg[u]);
+            gg[u][0] = in ? ld_stream(a.g0 + k) : T(0);
+            gg[u][1] = in ? ld_stream(a.g1 + k) : T(0);
+            if constexpr (D == 3) gg[u][2] = in ? ld_stream(a.g2 + k) : T(0);
         }
         T Pj[kUnroll][D][D];
 #pragma unroll
@@ -715,10 +691,8 @@ StepArgs<T> make_step_args(srdr_body* b)
     a.sell_ptr = b->sell_ptr;
     a.sell_col = b->sell_col;
     a.g0 = static_cast<const T*>(b->sell_g);
-    a.g1 = a.g0 ? a.g0 + b->nslots : nullptr;
-    a.g2 = a.g1 ? a.g1 + b->nslots : nullptr;
-    a.gq = b->sell_gq;
-    a.gunit = b->gunit;
+    a.g1 = a.g0 + b->nslots;
+    a.g2 = a.g1 + b->nslots;
     a.cpos = static_cast<const T*>(b->cpos);
     a.ccell = b->ccell;
     a.B0 = static_cast<const T*>(b->B0);

@@ -615,54 +615,6 @@ __global__ void k_sell_fill(int n, const int* __restrict__ row_ptr, const int* _
     }
 }
 
-// sliced ELL of the FP32 3D passes: per slot the neighbour and its packed
-// pair gradient (gq_encode with the row's unit, the same formula as above
-// before packing), per row the unit, and G_i summed in FP64 in row order
-// from the decoded values (replacing k_gsum's), so the force sum's
-// difference form holds for the values the passes read
-__global__ void k_sell_fill_packed(int n, const int* __restrict__ row_ptr, const int* __restrict__ col,
-                                   const int* __restrict__ sell_ptr, const float* __restrict__ cpos,
-                                   const int* __restrict__ ccell, float rc, float inv_h, float kc,
-                                   int* __restrict__ scol, unsigned long long* __restrict__ sgq,
-                                   float* __restrict__ gunit, float* __restrict__ Gs)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int s = i >> 5, lane = i & 31;
-    int base = sell_ptr[s], width = (sell_ptr[s + 1] - base) >> 5;
-    int k0 = row_ptr[i], deg = row_ptr[i + 1] - k0;
-    const vec4_t<float> pi = load_cpos<float>(cpos, i);
-    const int ci = ccell[i];
-    float mx = 0.f;
-    for (int t = 0; t < deg; ++t) {
-        const int j = col[k0 + t];
-        float gg[3];
-        PairG<float>::template g<3>(pi, ci, load_cpos<float>(cpos, j), ccell[j], rc, inv_h, kc, gg);
-        for (int q = 0; q < 3; ++q) mx = fmaxf(mx, fabsf(gg[q]));
-    }
-    int e = 0;
-    frexpf(mx, &e);  // mx = f 2^e, 1/2 <= f < 1: every |component| < 2^e
-    const float unit = ldexpf(1.f, e - 20), inv = ldexpf(1.f, 20 - e);
-    double G[3] = {0, 0, 0};
-    for (int t = 0; t < width; ++t) {
-        const int64_t slot = (int64_t)base + t * 32 + lane;
-        unsigned long long w = 0;
-        int j = i;
-        if (t < deg) {
-            j = col[k0 + t];
-            float gg[3], d[3];
-            PairG<float>::template g<3>(pi, ci, load_cpos<float>(cpos, j), ccell[j], rc, inv_h, kc, gg);
-            w = gq_encode(gg, inv);
-            gq_decode(w, unit, d);
-            for (int q = 0; q < 3; ++q) G[q] += (double)d[q];
-        }
-        scol[slot] = j;
-        sgq[slot] = w;
-    }
-    gunit[i] = unit;
-    for (int q = 0; q < 3; ++q) Gs[(size_t)q * n + i] = (float)G[q];
-}
-
 __global__ void k_foot_stats(const int* __restrict__ start, int ncells, int dim, int nx, int ny,
                              int nz, const int* __restrict__ row_ptr, int* __restrict__ out)
 {
@@ -960,25 +912,15 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
     b->nslots = nslots;
     const int64_t ns = std::max(nslots, 1);
     SRDR_TRY(dalloc(b, &b->sell_col, ns));
-    if (sizeof(T) == 4 && dim == 3) {
-        // FP32 3D: packed pair gradients, 8 bytes a slot instead of 12
-        SRDR_TRY(dalloc(b, &b->sell_gq, ns));
-        SRDR_TRY(dalloc(b, &b->gunit, n));
-        k_sell_fill_packed<<<nblocks(n), kThreads, 0, st>>>(
-            n, b->row_ptr, b->col, b->sell_ptr, reinterpret_cast<const float*>(cpos), b->ccell,
-            (float)b->rc, (float)(1.0 / b->h), (float)kernel_kc(dim, b->h), b->sell_col, b->sell_gq,
-            b->gunit, reinterpret_cast<float*>(Gs));
-    } else {
-        T* sg = nullptr;
-        SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
-        b->sell_g = sg;
-        if (dim == 2)
-            k_sell_fill<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos,
-                                                               b->ccell, rcT, ihT, kcT, b->sell_col, sg, ns);
-        else
-            k_sell_fill<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos,
-                                                               b->ccell, rcT, ihT, kcT, b->sell_col, sg, ns);
-    }
+    T* sg = nullptr;
+    SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
+    b->sell_g = sg;
+    if (dim == 2)
+        k_sell_fill<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
+                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
+    else
+        k_sell_fill<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
+                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
 
     // footprint maxima size the damping sweep's shared memory
     int* fs = nullptr;
@@ -1219,9 +1161,7 @@ __global__ void k_bsell_fill(const BrickInfo* __restrict__ info, const int* __re
                              const int* __restrict__ col, const int* __restrict__ cell_of,
                              const int* __restrict__ bsell_ptr, const T* __restrict__ cpos,
                              const int* __restrict__ ccell, T rc, T inv_h, T kc,
-                             uint16_t* __restrict__ lidx, T* __restrict__ sg, int64_t nslots,
-                             const int* __restrict__ sell_ptr, const unsigned long long* __restrict__ sgq,
-                             const float* __restrict__ gunit)
+                             uint16_t* __restrict__ lidx, T* __restrict__ sg, int64_t nslots)
 {
     __shared__ HaloRows h;
     const BrickInfo bi = info[blockIdx.x];
@@ -1255,14 +1195,7 @@ __global__ void k_bsell_fill(const BrickInfo* __restrict__ info, const int* __re
                 const int r = (cz - g.hz0) * h.hny + (cy - g.hy0);
                 l = h.hoff[r] + (j - h.hst[r]);
                 T gg[D];
-                if (sgq) {
-                    // FP32 3D: the sliced-ELL layout's decoded value, bit for bit
-                    float x[3];
-                    gq_decode(sgq[(int64_t)sell_ptr[i >> 5] + t * 32 + (i & 31)], gunit[i], x);
-                    for (int q = 0; q < D; ++q) gg[q] = (T)x[q];
-                } else {
-                    PairG<T>::template g<D>(pi, ci, load_cpos<T>(cpos, j), ccell[j], rc, inv_h, kc, gg);
-                }
+                PairG<T>::template g<D>(pi, ci, load_cpos<T>(cpos, j), ccell[j], rc, inv_h, kc, gg);
                 for (int q = 0; q < D; ++q) gq[q] = gg[q];
             }
             lidx[slot] = (uint16_t)l;
@@ -1351,12 +1284,12 @@ srdr_status build_bricks_typed(srdr_body* b)
         k_bsell_fill<T, 2><<<nbk, 128, 0, st>>>(b->binfo, b->cell_start, b->nc[0], b->nc[1], b->nc[2], d,
                                                 b->bown, b->bown_h, b->row_ptr, b->col, b->cell_of,
                                                 b->bsell_ptr, static_cast<const T*>(b->cpos), b->ccell, rcT,
-                                                ihT, kcT, b->blidx, sg, ns, b->sell_ptr, b->sell_gq, b->gunit);
+                                                ihT, kcT, b->blidx, sg, ns);
     else
         k_bsell_fill<T, 3><<<nbk, 128, 0, st>>>(b->binfo, b->cell_start, b->nc[0], b->nc[1], b->nc[2], d,
                                                 b->bown, b->bown_h, b->row_ptr, b->col, b->cell_of,
                                                 b->bsell_ptr, static_cast<const T*>(b->cpos), b->ccell, rcT,
-                                                ihT, kcT, b->blidx, sg, ns, b->sell_ptr, b->sell_gq, b->gunit);
+                                                ihT, kcT, b->blidx, sg, ns);
     SRDR_CK(cudaGetLastError());
     SRDR_TRY(dalloc(b, &b->ke_pp, b->n));
     SRDR_CK(cudaStreamSynchronize(st));

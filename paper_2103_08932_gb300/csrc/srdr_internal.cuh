@@ -104,34 +104,6 @@ __device__ inline void lo_decode(const float (&h)[3], float packed, float (&l)[3
     }
 }
 
-// Packed pair gradient of the FP32 3D passes' stream: the three components
-// of g_ij as signed 21-bit multiples of the row's unit 2^(e_i - 20), where
-// |g_ij| < 2^e_i for every entry of row i.  One 8-byte stream word per slot
-// instead of three 4-byte components; each component is off by at most half
-// a unit (about 5e-7 of the row's largest component), and every decoded
-// value is an exact FP32 number, so G_i = sum_j g_ij summed from the decoded
-// values keeps the force sum's difference form exact.  The value 0 decodes
-// to g = 0 (padding slots).
-__device__ inline unsigned long long gq_encode(const float (&g)[3], float inv_unit)
-{
-    unsigned long long w = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        int q = __float2int_rn(g[c] * inv_unit);
-        q = q > 1048575 ? 1048575 : (q < -1048575 ? -1048575 : q);
-        w |= (unsigned long long)((unsigned)q & 0x1FFFFFu) << (21 * c);
-    }
-    return w;
-}
-__device__ inline void gq_decode(unsigned long long w, float unit, float (&g)[3])
-{
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int q = (int)((long long)(w << (43 - 21 * c)) >> 43);  // sign-extended field c
-        g[c] = __fmul_rn((float)q, unit);
-    }
-}
-
 // 1/2 m |v|^2 of one particle with explicit roundings: the same bits in
 // every kernel that evaluates it (no contraction choice left to the
 // compiler)
@@ -170,8 +142,6 @@ struct StepArgs {
     const T* __restrict__ g0;   // [slots] V_j grad0_i W_ij, x component (sliced ELL)
     const T* __restrict__ g1;   // y component
     const T* __restrict__ g2;   // z component
-    const unsigned long long* __restrict__ gq;  // FP32 3D: [slots] packed g_ij (g0..g2 unused)
-    const float* __restrict__ gunit;            // FP32 3D: [n] unit of row i's packed components
     const T* __restrict__ cpos;   // [n][4] offset in its cell (x, y, z) and volume
     const int* __restrict__ ccell; // [n] packed cell coordinates x | y << 10 | z << 20
     const T* __restrict__ B0;   // [D*D][n]
@@ -284,9 +254,7 @@ struct srdr_body {
     int64_t nslots = 0;
     int* sell_ptr = nullptr;
     int* sell_col = nullptr;
-    void* sell_g = nullptr;     // T [3][slots] pair gradients in sliced-ELL order (FP64, 2D)
-    unsigned long long* sell_gq = nullptr;  // FP32 3D: [slots] packed pair gradients
-    float* gunit = nullptr;     // FP32 3D: [n] unit of each row's packed components
+    void* sell_g = nullptr;     // T [3][slots] pair gradients in sliced-ELL order
     void* cpos = nullptr;       // T [n][4] offset in its cell and volume
     int* ccell = nullptr;       // [n] packed cell coordinates
     void* B0 = nullptr;         // T [D*D][n]
