@@ -365,7 +365,13 @@ def test_sweep_sync_modes_are_bitwise_equal(spec, precision, damping, jit):
             b = gpu_for(spec, precision=precision, damping=damping, particles=parts)
             b.sweep_sync(mode)
             b.tune(g, w)
-            b.step(14)
+            try:
+                b.step(14)
+            except srdr.SrdrError as e:
+                # a mapping whose cells do not fit in shared memory is refused
+                # (the autotuner skips it); nothing else may fail
+                assert e.status == srdr.SRDR_ERR_INVALID and "shared memory" in str(e)
+                continue
             st = b.stats()
             if mode != srdr.SRDR_SWEEP_AUTO:
                 assert st["sweep_sync"] == mode
