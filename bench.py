@@ -481,20 +481,28 @@ def run_batched_solves(nbodies, cap, tol=1e-8, seed=3):
     from paper_2103_08932_gb300 import synth as S
     specs = S.random_bodies(256, 1e3, 2e5, seed)[:nbodies]
     descs = [srdr.make_desc(s, precision=srdr.SRDR_FP32_MIXED) for s in specs]
-    bodies = [srdr.Body(d) for d in descs]
-    n_total = sum(b.n for b in bodies)
-    batch = srdr.Batch(bodies)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    status, per, steps_b = batch.run(tol, cap)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    info = batch.info()
-    batch.close()
-    conv_b = [int(x) == 0 for x in per]
-    u_b = [b.displacement() for b in bodies]
-    for b in bodies:
-        b.close()
+    runs = {}
+    for name, mode in (("shared", srdr.SRDR_BATCH_SHARED), ("streams", srdr.SRDR_BATCH_STREAMS)):
+        bodies = [srdr.Body(d) for d in descs]
+        n_total = sum(b.n for b in bodies)
+        batch = srdr.Batch(bodies)
+        batch.mode(mode)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status, per, steps_b = batch.run(tol, cap)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        info = batch.info()
+        batch.close()
+        runs[name] = {"t": t_batch, "conv": [int(x) == 0 for x in per], "steps": steps_b,
+                      "u": [b.displacement() for b in bodies], "n": [b.n for b in bodies], "info": info}
+        for b in bodies:
+            b.close()
+    t_batch = runs["streams"]["t"]
+    conv_b = runs["streams"]["conv"]
+    steps_b = runs["streams"]["steps"]
+    u_b = runs["streams"]["u"]
+    info = runs["shared"]["info"]
     t_alone = 0.0
     conv_a, steps_a, same = [], [], 0
     for k, d in enumerate(descs):
@@ -508,19 +516,23 @@ def run_batched_solves(nbodies, cap, tol=1e-8, seed=3):
         steps_a.append(steps)
         same += int(np.array_equal(b.displacement(), u_b[k]))
         b.close()
-    ps_b = sum(int(s) * d.n for s, d in zip(steps_b, bodies))
+    ps_b = sum(int(s) * n for s, n in zip(steps_b, runs["streams"]["n"]))
+    same_shared = sum(int(np.array_equal(a, b)) for a, b in zip(runs["shared"]["u"], u_b))
+    t_sh = runs["shared"]["t"]
     return {"workload": f"first {nbodies} bodies of the 256-body batched workload (seed {seed}; "
                         f"{n_total} particles), FP32-mixed, KE/KE_max < {tol:g}, cap {cap} steps",
             "bodies": CONFIG4_NOTE,
             "converged": sum(conv_b), "not_converged": nbodies - sum(conv_b),
-            "batched_s": t_batch, "one_at_a_time_s": t_alone,
+            "batched_mode": "streams (every body on its own stream, all at once)",
+            "batched_s": t_batch, "shared_launches_s": t_sh, "one_at_a_time_s": t_alone,
             "batched_solves_per_s": sum(conv_b) / t_batch,
+            "shared_launches_solves_per_s": sum(runs["shared"]["conv"]) / t_sh,
             "one_at_a_time_solves_per_s": sum(conv_a) / t_alone,
-            "speedup": t_alone / t_batch,
+            "speedup": t_alone / t_batch, "shared_launches_speedup": t_alone / t_sh,
             "batched_particle_steps_per_s": ps_b / t_batch,
             "steps_min_median_max": [int(min(steps_b)), int(np.median(steps_b)), int(max(steps_b))],
-            "bitwise_equal_to_alone": same,
-            "launches_per_step": info["launches"] / max(1, info["steps"]),
+            "bitwise_equal_to_alone": same, "shared_bitwise_equal_to_streams": same_shared,
+            "shared_launches_per_step": info["launches"] / max(1, info["steps"]),
             "sweep_cells_per_warp": info["sweep_cells_per_warp"]}
 
 
@@ -559,10 +571,12 @@ def run_served(rate, count, n_lo, n_hi, tol, max_steps, seed=4, workload_note=No
     return out
 
 
-def run_block(steps):
+def run_block(steps, tol=1e-8, cap=20000):
     """The 0.1 m neo-Hookean cube at dp = 0.8 mm (125^3 body particles plus
     3 fixed and 3 prescribed layers, 2.05 M particles), top face at -10 %:
-    FP32-mixed against an all-FP64 GPU run of the same steps."""
+    FP32-mixed against an all-FP64 GPU run of the same steps, then both
+    relaxed to KE/KE_max < tol (the FP32-mixed state compared at the FP64
+    run's stopping step)."""
     import torch
 
     from paper_2103_08932_gb300 import srdr
@@ -591,6 +605,26 @@ def run_block(steps):
     moved = us["fp64"] - S.lattice(spec)[2]  # displacement from the initial field
     out["max_rel_displacement_error_fp32_vs_fp64"] = float(np.abs(d).max() / np.abs(us["fp64"]).max())
     out["max_rel_error_of_displacement_change"] = float(np.abs(d).max() / max(np.abs(moved).max(), 1e-300))
+    # relaxed to the KE criterion
+    rel = {}
+    for name, prec in (("fp64", srdr.SRDR_FP64), ("fp32_mixed", srdr.SRDR_FP32_MIXED)):
+        b = srdr.Body(srdr.make_desc(spec, precision=prec))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, nsteps, ratio = b.relax(tol, cap, check=False)
+        torch.cuda.synchronize()
+        rel[name] = {"status": srdr.STATUS_NAMES.get(st, st), "steps": nsteps, "ke_ratio": ratio,
+                     "seconds": time.perf_counter() - t0, "damped_steps": b.stats()["damped_steps"]}
+        if name == "fp32_mixed" and nsteps != rel["fp64"]["steps"]:
+            b.close()
+            b = srdr.Body(srdr.make_desc(spec, precision=prec))
+            b.step(rel["fp64"]["steps"])
+        us[name] = b.displacement()
+        b.close()
+    d = us["fp32_mixed"] - us["fp64"]
+    rel["max_rel_displacement_error_fp32_vs_fp64_at_fp64_stop"] = float(np.abs(d).max() / np.abs(us["fp64"]).max())
+    rel["max_displacement_m"] = float(np.abs(us["fp64"]).max())
+    out["relaxed"] = rel
     return out
 
 
