@@ -124,7 +124,22 @@ typedef struct {
     double dt;
     double twist[4];
     int sweep_layout;
+    int pass_layout;    /* SRDR_PASS_LAYOUT_AUTO (0) or SRDR_PASS_LAYOUT_SELL, see below */
 } srdr_body_desc;
+
+/* pass_layout: how the stress and force passes (Secs. 2.2-2.3, the momentum
+ *   equation) enumerate a particle's neighbours.
+ *   SRDR_PASS_LAYOUT_AUTO (0): a body whose reference positions form a box
+ *   lattice of spacing dp (x fastest, then y, then z: the order that
+ *   srdr_body_create builds), with one particle volume, takes the lattice
+ *   stencil (SRDR_PASS_STENCIL below) when the stencil reproduces every
+ *   particle's neighbour list (checked at creation); any other body takes
+ *   the sliced-ELL mapping.  SRDR_PASS_LAYOUT_SELL: the sliced-ELL mapping
+ *   (and the brick mapping of srdr_body_pass_mapping) for every body.  The
+ *   pair gradients of the stencil are evaluated once per lattice offset from
+ *   the exact offset, those of the sliced-ELL layout once per pair from the
+ *   positions: the two agree to rounding. */
+enum { SRDR_PASS_LAYOUT_AUTO = 0, SRDR_PASS_LAYOUT_SELL = 1 };
 
 typedef struct srdr_body srdr_body;
 
@@ -180,8 +195,9 @@ typedef struct {
     int converged;         /* last relax met its criterion */
     int64_t launches;      /* kernels launched by step / relax calls since creation */
     int sweep_cells_per_warp; /* damping-sweep mapping picked by the autotuner (1, 2, 4) */
-    int pass_mapping;      /* mapping the stress and force passes use: SRDR_PASS_SELL or
-                              SRDR_PASS_BRICKS (SRDR_PASS_AUTO before the first step) */
+    int pass_mapping;      /* mapping the stress and force passes use: SRDR_PASS_STENCIL,
+                              SRDR_PASS_SELL or SRDR_PASS_BRICKS (SRDR_PASS_AUTO before
+                              the first step of a body without the stencil) */
     int sweep_sync;        /* synchronisation of the sweep's colour phases in use:
                               SRDR_SWEEP_CELLS or SRDR_SWEEP_BARRIER (SRDR_SWEEP_AUTO
                               before the first damped step) */
@@ -271,8 +287,16 @@ srdr_status srdr_body_debug_stall_sweep(srdr_body* body);
  * sliced-ELL mapping, measured faster on GB300 for every body tried (the
  * brick layout is then not built).  Both visit a row's neighbours in the
  * same order with the same roundings, so results are bitwise the same; the
- * choice changes speed only. */
-enum { SRDR_PASS_AUTO = 0, SRDR_PASS_SELL = 1, SRDR_PASS_BRICKS = 2 };
+ * choice changes speed only.  SRDR_PASS_STENCIL is the mapping of bodies that
+ * took the lattice stencil at creation (pass_layout above): neighbour k of
+ * the particle at lattice point p is the particle at p + o_k when that point
+ * lies in the box, with the pair gradient of offset o_k from a table; no
+ * neighbour stream is read, and a warp's 32 threads are consecutive lattice
+ * points, so a warp's gathers of one offset are consecutive records.  Such a
+ * body keeps its particle arrays in lattice order and refuses the other two
+ * mappings (SRDR_ERR_INVALID); create it with pass_layout =
+ * SRDR_PASS_LAYOUT_SELL to use them. */
+enum { SRDR_PASS_AUTO = 0, SRDR_PASS_SELL = 1, SRDR_PASS_BRICKS = 2, SRDR_PASS_STENCIL = 3 };
 srdr_status srdr_body_pass_mapping(srdr_body* body, int mapping, int brick_x, int brick_y,
                                    int brick_z);
 srdr_status srdr_body_kernel_times(const srdr_body* body, srdr_kernel_times* out);
@@ -319,8 +343,10 @@ srdr_status srdr_batch_run(srdr_batch* batch, double ke_ratio, int64_t max_steps
  * where shared launches make every body wait at every step for the slowest
  * damped body.  SRDR_BATCH_AUTO (the default) is SRDR_BATCH_STREAMS, measured
  * faster on GB300 (2x to 4.5x on uneven bodies).  Results are bitwise the same
- * in every mode and equal to the bodies relaxed alone.  SRDR_ERR_INVALID for
- * another mode. */
+ * in every mode and equal to the bodies relaxed alone.  SRDR_BATCH_SHARED
+ * takes sliced-ELL bodies only (bodies created with pass_layout =
+ * SRDR_PASS_LAYOUT_SELL, or not on a box lattice); a batch holding a
+ * lattice-stencil body refuses it.  SRDR_ERR_INVALID for another mode. */
 enum { SRDR_BATCH_AUTO = 0, SRDR_BATCH_SHARED = 1, SRDR_BATCH_STREAMS = 2 };
 srdr_status srdr_batch_mode(srdr_batch* batch, int mode);
 /* Steps run, kernels launched, and the autotuner's choices (damping-sweep

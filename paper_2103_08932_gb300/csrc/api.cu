@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
 #include <new>
 #include <vector>
 
@@ -133,7 +135,44 @@ srdr_status check_desc(const srdr_body_desc* d)
         set_error("unknown sweep layout %d", d->sweep_layout);
         return SRDR_ERR_INVALID;
     }
+    if (d->pass_layout != SRDR_PASS_LAYOUT_AUTO && d->pass_layout != SRDR_PASS_LAYOUT_SELL) {
+        set_error("unknown pass layout %d", d->pass_layout);
+        return SRDR_ERR_INVALID;
+    }
     return SRDR_OK;
+}
+
+// Box lattice of spacing dp in x-fastest order (the order srdr_body_create
+// builds): lx points along x, then ly rows, then lz planes, every position
+// within 1e-9 dp of r0[0] + (ix, iy, iz) dp and one volume.  Returns false
+// for any other particle set.
+bool detect_lattice(const srdr_body_desc* d, int64_t n, const double* r0, const double* vol, int lat[3])
+{
+    lat[0] = lat[1] = lat[2] = 0;
+    if (n < 1 || n > INT32_MAX) return false;
+    const int dim = d->dim;
+    const double dp = d->dp, tol = 1e-9 * dp;
+    auto same = [&](int64_t i, int64_t j, int a) { return std::fabs(r0[i * 3 + a] - r0[j * 3 + a]) <= tol; };
+    int64_t nx = 1;
+    while (nx < n && same(nx, 0, 1) && (dim == 2 || same(nx, 0, 2))) ++nx;
+    int64_t np = nx;
+    if (dim == 3)
+        while (np < n && same(np, 0, 2)) ++np;
+    else
+        np = n;
+    if (np % nx != 0 || n % np != 0) return false;
+    const int64_t ny = np / nx, nz = n / np;
+    if (dim == 2 && nz != 1) return false;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t c[3] = {i % nx, (i / nx) % ny, i / np};
+        for (int a = 0; a < dim; ++a)
+            if (std::fabs(r0[i * 3 + a] - (r0[a] + (double)c[a] * dp)) > tol) return false;
+        if (vol && vol[i] != vol[0]) return false;
+    }
+    lat[0] = (int)nx;
+    lat[1] = (int)ny;
+    lat[2] = (int)nz;
+    return true;
 }
 
 // time step: 0.6 min(h / c, sqrt(h / |a|max)) with c = sqrt(K / rho0)
@@ -224,6 +263,7 @@ srdr_status create_common(const srdr_body_desc* desc, int64_t n, const double* r
     if (flags)
         for (int64_t i = 0; i < n && !has_end; ++i) has_end = (flags[i] & SRDR_FLAG_END_LOAD) != 0;
     b->dt = desc->dt > 0 ? desc->dt : auto_dt(b, has_end, n, r0, flags);
+    if (desc->pass_layout == SRDR_PASS_LAYOUT_AUTO) detect_lattice(desc, n, r0, vol, b->lat);
 
     srdr_status st = dalloc(b, &b->sc, 1);
     if (st == SRDR_OK) {
@@ -302,7 +342,7 @@ __global__ void k_read_uv(const int* __restrict__ perm, int n, const double* __r
     (void)ulo;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int i = perm[s];
+    const int i = perm ? perm[s] : s;  // null: arrays in original order
     float hf[3] = {0, 0, 0}, lf[3] = {0, 0, 0};
     if (!u) {
         const float4 r = reinterpret_cast<const float4*>(uhi)[s];
@@ -332,7 +372,7 @@ __global__ void k_write_uv(const int* __restrict__ perm, int n, const double* __
     (void)ulo;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int i = perm[s];
+    const int i = perm ? perm[s] : s;  // null: arrays in original order
     float h[3] = {0, 0, 0}, l[3] = {0, 0, 0};
     for (int a = 0; a < 3; ++a) {
         double vv = vin ? vin[(size_t)i * 3 + a] : (double)v[(size_t)s * 4 + a];
@@ -356,7 +396,7 @@ __global__ void k_read_field(const int* __restrict__ perm, int n, int dim, const
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int i = perm[s];
+    const int i = perm ? perm[s] : s;  // null: arrays in original order
     for (int p = 0; p < 3; ++p)
         for (int q = 0; q < 3; ++q) {
             double x = 0.0;
@@ -491,10 +531,10 @@ static srdr_status read_uv(const srdr_body* b, double* out, size_t nd, int what)
     SRDR_TRY(dalloc(m, &d, (size_t)b->n * 3));
     int nb = (int)((b->n + 255) / 256);
     if (b->prec == SRDR_FP64)
-        k_read_uv<double><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, b->u, nullptr, nullptr,
+        k_read_uv<double><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, b->u, nullptr, nullptr,
                                                      (const double*)b->v, 0.5 * b->dt, what, d);
     else
-        k_read_uv<float><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, nullptr, b->uhi, b->ulo,
+        k_read_uv<float><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, nullptr, b->uhi, b->ulo,
                                                     (const float*)b->v, 0.5 * b->dt, what, d);
     SRDR_CK(cudaGetLastError());
     SRDR_CK(cudaMemcpyAsync(out, d, sizeof(double) * 3 * b->n, cudaMemcpyDeviceToHost, b->stream));
@@ -535,18 +575,18 @@ srdr_status srdr_body_write_state(srdr_body* b, const double* u, const double* v
         double* cur = nullptr;
         SRDR_TRY(dalloc(b, &cur, (size_t)b->n * 3));
         if (b->prec == SRDR_FP64)
-            k_read_uv<double><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, b->u, nullptr, nullptr,
+            k_read_uv<double><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, b->u, nullptr, nullptr,
                                                          (const double*)b->v, 0.5 * b->dt, 0, cur);
         else
-            k_read_uv<float><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, nullptr, b->uhi, b->ulo,
+            k_read_uv<float><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, nullptr, b->uhi, b->ulo,
                                                         (const float*)b->v, 0.5 * b->dt, 0, cur);
         du = cur;
     }
     if (b->prec == SRDR_FP64)
-        k_write_uv<double><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, du, dv, 0.5 * b->dt, b->u,
+        k_write_uv<double><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, du, dv, 0.5 * b->dt, b->u,
                                                       nullptr, nullptr, (double*)b->v);
     else
-        k_write_uv<float><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, du, dv, 0.5 * b->dt, nullptr,
+        k_write_uv<float><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, du, dv, 0.5 * b->dt, nullptr,
                                                      b->uhi, b->ulo, (float*)b->v);
     SRDR_CK(cudaGetLastError());
     SRDR_CK(cudaStreamSynchronize(b->stream));
@@ -594,7 +634,9 @@ srdr_status srdr_body_stats(const srdr_body* b, srdr_stats* out)
     out->converged = b->converged;
     out->launches = b->launches;
     out->sweep_cells_per_warp = b->sweep_cells_per_warp;
-    out->pass_mapping = b->pass_tiled < 0 ? SRDR_PASS_AUTO : (b->pass_tiled ? SRDR_PASS_BRICKS : SRDR_PASS_SELL);
+    out->pass_mapping = b->stencil ? SRDR_PASS_STENCIL
+                                   : (b->pass_tiled < 0 ? SRDR_PASS_AUTO
+                                                        : (b->pass_tiled ? SRDR_PASS_BRICKS : SRDR_PASS_SELL));
     out->sweep_sync = !b->sweep_tuned ? SRDR_SWEEP_AUTO : (b->sweep_cellwise ? SRDR_SWEEP_CELLS : SRDR_SWEEP_BARRIER);
     return SRDR_OK;
 }
@@ -662,11 +704,19 @@ srdr_status srdr_body_debug_stall_sweep(srdr_body* b)
 
 srdr_status srdr_body_pass_mapping(srdr_body* b, int mapping, int bx, int by, int bz)
 {
-    if (!b || mapping < SRDR_PASS_AUTO || mapping > SRDR_PASS_BRICKS || bx < 0 || bx > 4 || by < 0 ||
+    if (!b || mapping < SRDR_PASS_AUTO || mapping > SRDR_PASS_STENCIL || bx < 0 || bx > 4 || by < 0 ||
         by > 4 || bz < 0 || bz > 4) {
-        set_error("pass mapping must be SRDR_PASS_AUTO, _SELL or _BRICKS with brick sizes 0..4");
+        set_error("pass mapping must be SRDR_PASS_AUTO, _SELL, _BRICKS or _STENCIL with brick sizes 0..4");
         return SRDR_ERR_INVALID;
     }
+    if (b->stencil != (mapping == SRDR_PASS_STENCIL) && mapping != SRDR_PASS_AUTO) {
+        set_error(b->stencil ? "the body took the lattice stencil at creation (its arrays are in lattice "
+                               "order): create it with pass_layout = SRDR_PASS_LAYOUT_SELL for this mapping"
+                             : "the lattice stencil is chosen at creation (pass_layout = "
+                               "SRDR_PASS_LAYOUT_AUTO, a box lattice)");
+        return SRDR_ERR_INVALID;
+    }
+    if (b->stencil) return SRDR_OK;
     if (mapping == SRDR_PASS_BRICKS && b->desc.sweep_layout != SRDR_SWEEP_LAYOUT_3D) {
         set_error("brick-tiled passes need the 3^d-colour sweep layout (bricks of cells of edge r_c)");
         return SRDR_ERR_INVALID;
@@ -801,10 +851,10 @@ srdr_status srdr_body_read_field(const srdr_body* b, int field, double* out, siz
     const void* src = field == SRDR_FIELD_PB ? b->PB : b->B0;
     int stride = field == SRDR_FIELD_PB ? b->pb_stride : 0;
     if (b->prec == SRDR_FP64)
-        k_read_field<double><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, b->dim,
+        k_read_field<double><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, b->dim,
                                                         (const double*)src, stride, d);
     else
-        k_read_field<float><<<nb, 256, 0, b->stream>>>(b->perm, (int)b->n, b->dim,
+        k_read_field<float><<<nb, 256, 0, b->stream>>>(b->io_perm(), (int)b->n, b->dim,
                                                        (const float*)src, stride, d);
     SRDR_CK(cudaGetLastError());
     SRDR_CK(cudaMemcpyAsync(out, d, sizeof(double) * 9 * b->n, cudaMemcpyDeviceToHost, b->stream));

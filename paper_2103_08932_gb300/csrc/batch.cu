@@ -393,10 +393,11 @@ SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
     s.rec = static_cast<const SweepSlot<T>*>(b->srec);
-    s.mass = static_cast<const T*>(b->mass);
+    s.mass = static_cast<const T*>(b->stencil ? b->mass_sw : b->mass);
     s.sbm = static_cast<const T*>(b->sbm);
     s.srd = static_cast<const T*>(b->srd);
     s.v = static_cast<T*>(b->v);
+    s.pidx = b->pidx;
     s.sc = b->sc;
     s.c = b->desc.alpha > 0 ? (T)(b->eta / b->desc.alpha * b->dt) : T(0);
     s.pairwise = b->desc.damping == SRDR_DAMP_PAIRWISE;
@@ -1046,6 +1047,13 @@ srdr_status srdr_batch_mode(srdr_batch* bt, int mode)
         set_error("batch mode must be SRDR_BATCH_AUTO, _SHARED or _STREAMS");
         return SRDR_ERR_INVALID;
     }
+    if (mode == SRDR_BATCH_SHARED)
+        for (const srdr_body* b : bt->bodies)
+            if (b->stencil) {
+                set_error("shared launches take sliced-ELL bodies only: create the batch's bodies with "
+                          "pass_layout = SRDR_PASS_LAYOUT_SELL");
+                return SRDR_ERR_INVALID;
+            }
     bt->mode = mode;
     return SRDR_OK;
 }

@@ -321,13 +321,81 @@ __device__ inline void pass_a_particle(const StepArgs<T>& a, int i)
     pass_a_epilogue<T, D, MAT>(a, i, G);
 }
 
+// ------------------------------------------------------------------ lattice stencil
+// A body on a box lattice has the same neighbour offsets at every particle
+// away from its faces, and the same pair gradient for every pair with the
+// same offset (g_ij depends on r0_ij only, Eq. correction-matrix1, with one
+// particle volume).  Neighbour k of particle i is then j = i + delta_k when
+// the lattice point of j lies in the box; the offsets are ordered by delta,
+// i.e. by ascending neighbour index, the order of the neighbour lists, and
+// the set-up checks that the stencil reproduces every particle's list.  An
+// offset that leaves the box (and the zero padding of the table) takes j = i,
+// whose difference terms below are exactly zero.  No neighbour stream is
+// read; the 32 threads of a warp are consecutive lattice points, so their
+// gathers of one offset are consecutive records.
+static_assert(kUnroll == kStencilBatch, "stencil tables are padded to the passes' batch");
+
+template <typename T, int D>
+__device__ inline void stencil_slots(const StepArgs<T>& a, int i, int x, int y, int z, int k0,
+                                     int (&jj)[kUnroll], T (&gg)[kUnroll][D])
+{
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int4 o = __ldg(a.st_off + k0 + u);
+        const bool in = (unsigned)(x + o.x) < (unsigned)a.lx && (unsigned)(y + o.y) < (unsigned)a.ly &&
+                        (unsigned)(z + o.z) < (unsigned)a.lz;
+        jj[u] = in ? i + o.w : i;
+        const vec4_t<T> g = load_cpos<T>(a.st_g, k0 + u);
+        gg[u][0] = g.x;
+        gg[u][1] = g.y;
+        if constexpr (D == 3) gg[u][2] = g.z;
+    }
+}
+
+__device__ inline void lattice_xyz(int i, int lx, int ly, int& x, int& y, int& z)
+{
+    const int r = i / lx;
+    x = i - r * lx;
+    z = r / ly;
+    y = r - z * ly;
+}
+
 template <typename T, int D, int MAT>
+__device__ inline void pass_a_particle_st(const StepArgs<T>& a, int i)
+{
+    int x, y, z;
+    lattice_xyz(i, a.lx, a.ly, x, y, z);
+    T xi[3], li[3];
+    UAcc<T>::load(a.u, a.uhi, a.ulo, i, xi, li);
+    T G[D][D];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) G[p][q] = 0;
+    for (int k0 = 0; k0 < a.st_k; k0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
+        stencil_slots<T, D>(a, i, x, y, z, k0, jj, gg);
+        T xj[kUnroll][3], lj[kUnroll][3];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) UAcc<T>::load(a.u, a.uhi, a.ulo, jj[u], xj[u], lj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) acc_grad<T, D>(G, xi, li, xj[u], lj[u], gg[u]);
+    }
+    pass_a_epilogue<T, D, MAT>(a, i, G);
+}
+
+// ST: the lattice stencil instead of the sliced-ELL stream
+template <typename T, int D, int MAT, int ST>
 __global__ void __launch_bounds__(kThreads) k_pass_a(StepArgs<T> a)
 {
     if (a.sc->done) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    pass_a_particle<T, D, MAT>(a, i);
+    if constexpr (ST)
+        pass_a_particle_st<T, D, MAT>(a, i);
+    else
+        pass_a_particle<T, D, MAT>(a, i);
 }
 
 // ------------------------------------------------------------------ reductions
@@ -594,12 +662,41 @@ __device__ inline double pass_b_particle(const StepArgs<T>& a, int i, int final_
 }
 
 template <typename T, int D>
+__device__ inline double pass_b_particle_st(const StepArgs<T>& a, int i, int final_step)
+{
+    int x, y, z;
+    lattice_xyz(i, a.lx, a.ly, x, y, z);
+    T Pi[D][D];
+    PBL<T, D>::load(a.PB, a.n, i, Pi);
+    T acc[D];
+#pragma unroll
+    for (int p = 0; p < D; ++p) acc[p] = 0;
+    for (int k0 = 0; k0 < a.st_k; k0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
+        stencil_slots<T, D>(a, i, x, y, z, k0, jj, gg);
+        T Pj[kUnroll][D][D];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, a.n, jj[u], Pj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) acc_force<T, D>(acc, Pi, Pj[u], gg[u]);
+    }
+    return pass_b_epilogue<T, D>(a, i, acc, Pi, final_step);
+}
+
+template <typename T, int D, int ST>
 __global__ void __launch_bounds__(kThreads, 3) k_pass_b(StepArgs<T> a, int final_step)
 {
     if (a.sc->done) return;
     if (a.dflag) final_step = *a.dflag == 0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const double ke = i < a.n ? pass_b_particle<T, D>(a, i, final_step) : 0.0;
+    double ke = 0.0;
+    if (i < a.n) {
+        if constexpr (ST)
+            ke = pass_b_particle_st<T, D>(a, i, final_step);
+        else
+            ke = pass_b_particle<T, D>(a, i, final_step);
+    }
     if (final_step) ke_last_block(a, ke, 0);
 }
 
@@ -656,30 +753,34 @@ __global__ void k_decide_one(const DevScalars* sc, unsigned long long seed, doub
 // dv_i = dt (2 eta / m_i) sum_j V_i V_j (v_i - v_j) / r_ij dW/dr (Eq.
 // damping-term at v^n) over the sweep's CSR rows, w_ij = V_i V_j W'(r)/r;
 // the force pass adds it to v* (Sec. 3: the explicit scheme the split
-// random-choice scheme replaces)
+// random-choice scheme replaces).  Rows, columns and mass_s are in sorted
+// order; v and dv in particle order, reached through pidx when it is set.
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_visc(int n, const int* __restrict__ row_ptr,
                                                     const int* __restrict__ col, const T* __restrict__ w,
-                                                    const T* __restrict__ v, const T* __restrict__ mass,
-                                                    T c2eta_dt, T* __restrict__ dv, const DevScalars* sc)
+                                                    const T* __restrict__ v, const T* __restrict__ mass_s,
+                                                    const int* __restrict__ pidx, T c2eta_dt,
+                                                    T* __restrict__ dv, const DevScalars* sc)
 {
     if (sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const vec4_t<T> vi4 = ld_v4<T>(v, i);
+    const int pi = pidx ? __ldg(pidx + i) : i;
+    const vec4_t<T> vi4 = ld_v4<T>(v, pi);
     const T vi[3] = {vi4.x, vi4.y, vi4.z};
     T e[3] = {0, 0, 0};
     for (int k = __ldg(row_ptr + i); k < __ldg(row_ptr + i + 1); ++k) {
-        const vec4_t<T> vj4 = ld_v4<T>(v, __ldg(col + k));
+        const int j = __ldg(col + k);
+        const vec4_t<T> vj4 = ld_v4<T>(v, pidx ? __ldg(pidx + j) : j);
         const T vj[3] = {vj4.x, vj4.y, vj4.z};
         const T wk = __ldg(w + k);
 #pragma unroll
         for (int d = 0; d < D; ++d) e[d] = fma_t(wk, sub_t(vi[d], vj[d]), e[d]);
     }
-    const T s = c2eta_dt / mass[i];
+    const T s = c2eta_dt / mass_s[i];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) dv[(size_t)i * 4 + d] = d < D ? s * e[d] : T(0);
-    dv[(size_t)i * 4 + 3] = T(0);
+    for (int d = 0; d < 3; ++d) dv[(size_t)pi * 4 + d] = d < D ? s * e[d] : T(0);
+    dv[(size_t)pi * 4 + 3] = T(0);
 }
 
 // ------------------------------------------------------------------ host: kernel arguments
@@ -718,6 +819,14 @@ StepArgs<T> make_step_args(srdr_body* b)
     for (int p = 0; p < 3; ++p) {
         a.grav[p] = (T)(p < b->dim ? b->desc.gravity[p] : 0.0);
         a.endl[p] = (T)(p < b->dim ? b->desc.end_load[p] : 0.0);
+    }
+    if (b->stencil) {
+        a.st_off = b->st_off;
+        a.st_g = static_cast<const T*>(b->st_g);
+        a.st_k = b->st_k;
+        a.lx = b->lat[0];
+        a.ly = b->lat[1];
+        a.lz = b->lat[2];
     }
     return a;
 }

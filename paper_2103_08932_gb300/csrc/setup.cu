@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "srdr_internal.cuh"
@@ -711,6 +713,241 @@ srdr_status scan_exclusive(const int* in, int* out, int count, int* tmp, cudaStr
     return SRDR_OK;
 }
 
+// ------------------------------------------------------------------ lattice stencil
+// Lattice coordinates of particle index i of a box of lx x ly points per plane.
+__device__ inline void lat_xyz(int i, int lx, int ly, int& x, int& y, int& z)
+{
+    const int r = i / lx;
+    x = i - r * lx;
+    z = r / ly;
+    y = r - z * ly;
+}
+
+__device__ inline bool lat_in(const int4& o, int x, int y, int z, int lx, int ly, int lz)
+{
+    return (unsigned)(x + o.x) < (unsigned)lx && (unsigned)(y + o.y) < (unsigned)ly &&
+           (unsigned)(z + o.z) < (unsigned)lz;
+}
+
+// The neighbour list of sorted particle s (its CSR row, ascending original
+// index) against the stencil's in-box offsets in table order (zero offsets
+// are padding); the first difference sets *bad.
+__global__ void k_stencil_check(int n, const int* __restrict__ perm, const int* __restrict__ row_ptr,
+                                const int* __restrict__ col, const int4* __restrict__ off, int K, int lx,
+                                int ly, int lz, int* __restrict__ bad)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int i = perm[s];
+    int x, y, z;
+    lat_xyz(i, lx, ly, x, y, z);
+    int k = row_ptr[s];
+    const int k1 = row_ptr[s + 1];
+    for (int t = 0; t < K; ++t) {
+        const int4 o = off[t];
+        if ((o.x | o.y | o.z) == 0 || !lat_in(o, x, y, z, lx, ly, lz)) continue;
+        if (k >= k1 || perm[col[k]] != i + o.w) {
+            atomicExch(bad, 1);
+            return;
+        }
+        ++k;
+    }
+    if (k != k1) atomicExch(bad, 1);
+}
+
+// G_i = sum_j g_ij over the in-box offsets of particle i (lattice order), in
+// FP64 from the table values the passes use, in table order
+template <typename T, int D>
+__global__ void k_stencil_gsum(int n, const int4* __restrict__ off, const T* __restrict__ g, int K, int lx,
+                               int ly, int lz, T* __restrict__ Gs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int x, y, z;
+    lat_xyz(i, lx, ly, x, y, z);
+    double G[3] = {0, 0, 0};
+    for (int t = 0; t < K; ++t)
+        if (lat_in(off[t], x, y, z, lx, ly, lz))
+            for (int a = 0; a < D; ++a) G[a] += (double)g[(size_t)t * 4 + a];
+    for (int a = 0; a < 3; ++a) Gs[(size_t)a * n + i] = (T)G[a];
+}
+
+// sorted -> particle order: rows of w elements (dst row perm[s] = src row s)
+// and columns of an [m][n] array; index lists mapped through perm
+template <typename E>
+__global__ void k_perm_rows(const int* __restrict__ perm, int n, int w, const E* __restrict__ src,
+                            E* __restrict__ dst)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const size_t i = (size_t)perm[s];
+    for (int c = 0; c < w; ++c) dst[i * w + c] = src[(size_t)s * w + c];
+}
+
+template <typename E>
+__global__ void k_perm_cols(const int* __restrict__ perm, int n, int m, const E* __restrict__ src,
+                            E* __restrict__ dst)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int i = perm[s];
+    for (int c = 0; c < m; ++c) dst[(size_t)c * n + i] = src[(size_t)c * n + s];
+}
+
+__global__ void k_map_idx(const int* __restrict__ perm, int count, int* __restrict__ a)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < count) a[q] = perm[a[q]];
+}
+
+// The stencil of a lattice body (b->lat set by the create path): every
+// offset o with |o| dp below the cut-off, ordered by index delta (ascending
+// neighbour index), with the pair gradient of the neighbour rows (Eq.
+// correction-matrix1 with the Wendland C2 kernel, the formula of pairg.cuh)
+// evaluated once in FP64 at r0_ij = -o dp, padded with zero offsets to a
+// multiple of the passes' batch.  *ok is set when the stencil reproduces the
+// neighbour list of every particle.
+template <typename T>
+srdr_status try_stencil(srdr_body* b, double vol, bool* ok)
+{
+    *ok = false;
+    cudaStream_t st = b->stream;
+    const int dim = b->dim, lx = b->lat[0], ly = b->lat[1], lz = b->lat[2];
+    const double dp = b->desc.dp, cut = b->cut;
+    const int R = (int)std::floor(cut / dp) + 1;
+    struct Off {
+        int x, y, z;
+        long long d;
+    };
+    std::vector<Off> offs;
+    for (int dz = dim == 3 ? -R : 0; dz <= (dim == 3 ? R : 0); ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                if ((dx | dy | dz) == 0) continue;
+                const double r2 = ((double)dx * dx + (double)dy * dy + (double)dz * dz) * dp * dp;
+                if (!(r2 < cut * cut)) continue;
+                offs.push_back({dx, dy, dz, dx + (long long)lx * (dy + (long long)ly * dz)});
+            }
+    std::sort(offs.begin(), offs.end(), [](const Off& p, const Off& q) { return p.d < q.d; });
+    const int K = (int)((offs.size() + kStencilBatch - 1) / kStencilBatch * kStencilBatch);
+    if (K == 0 || K > 4096) return SRDR_OK;
+    std::vector<int4> ho(K, int4{0, 0, 0, 0});
+    std::vector<T> hg((size_t)K * 4, T(0));
+    const double kc = kernel_kc(dim, b->h);
+    for (size_t t = 0; t < offs.size(); ++t) {
+        const Off& o = offs[t];
+        if (o.d < INT32_MIN || o.d > INT32_MAX) return SRDR_OK;
+        ho[t] = int4{o.x, o.y, o.z, (int)o.d};
+        const double rx = -o.x * dp, ry = -o.y * dp, rz = -o.z * dp;
+        const double r = std::sqrt(rx * rx + ry * ry + rz * rz);
+        const double tt = std::max(1.0 - 0.5 * r / b->h, 0.0);
+        const double w = kc * tt * tt * tt * vol;
+        hg[t * 4 + 0] = (T)(w * rx);
+        hg[t * 4 + 1] = (T)(w * ry);
+        hg[t * 4 + 2] = (T)(dim == 3 ? w * rz : 0.0);
+    }
+    int4* doff = nullptr;
+    T* dg = nullptr;
+    int* bad = nullptr;
+    SRDR_TRY(dalloc(b, &doff, K));
+    SRDR_TRY(dalloc(b, &dg, (size_t)K * 4));
+    SRDR_TRY(dalloc(b, &bad, 1));
+    SRDR_CK(cudaMemcpyAsync(doff, ho.data(), sizeof(int4) * K, cudaMemcpyHostToDevice, st));
+    SRDR_CK(cudaMemcpyAsync(dg, hg.data(), sizeof(T) * 4 * K, cudaMemcpyHostToDevice, st));
+    SRDR_CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    const int n = (int)b->n;
+    k_stencil_check<<<nblocks(n), kThreads, 0, st>>>(n, b->perm, b->row_ptr, b->col, doff, K, lx, ly, lz, bad);
+    SRDR_CK(cudaGetLastError());
+    int hbad = 1;
+    SRDR_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SRDR_CK(cudaStreamSynchronize(st));
+    SRDR_TRY(dev_free(b, bad));
+    if (hbad) {
+        SRDR_TRY(dev_free(b, doff));
+        SRDR_TRY(dev_free(b, dg));
+        return SRDR_OK;
+    }
+    b->st_off = doff;
+    b->st_g = dg;
+    b->st_k = K;
+    *ok = true;
+    return SRDR_OK;
+}
+
+// Move the particle arrays of a stencil body from sorted to lattice (=
+// original) order: flags, masses (the sorted copy stays for the sweep),
+// 1/m, u, v, B0, body force, and G_i from the stencil; the 2^d layout's
+// touched lists become particle indices.  The sweep's structures (cells,
+// rows, slot records) stay in sorted order and reach the particle arrays
+// through pidx = perm.
+template <typename T>
+srdr_status relayout_stencil(srdr_body* b)
+{
+    cudaStream_t st = b->stream;
+    const int n = (int)b->n, nb = nblocks(n), dim = b->dim;
+    const int* perm = b->perm;
+    uint8_t* fl = nullptr;
+    SRDR_TRY(dalloc(b, &fl, n));
+    k_perm_rows<uint8_t><<<nb, kThreads, 0, st>>>(perm, n, 1, b->flags, fl);
+    T *m = nullptr, *mi = nullptr, *v = nullptr, *B0 = nullptr;
+    SRDR_TRY(dalloc(b, &m, n));
+    SRDR_TRY(dalloc(b, &mi, n));
+    SRDR_TRY(dalloc(b, &v, (size_t)n * 4));
+    SRDR_TRY(dalloc(b, &B0, (size_t)n * dim * dim));
+    k_perm_rows<T><<<nb, kThreads, 0, st>>>(perm, n, 1, static_cast<const T*>(b->mass), m);
+    k_perm_rows<T><<<nb, kThreads, 0, st>>>(perm, n, 1, static_cast<const T*>(b->minv), mi);
+    k_perm_rows<T><<<nb, kThreads, 0, st>>>(perm, n, 4, static_cast<const T*>(b->v), v);
+    k_perm_cols<T><<<nb, kThreads, 0, st>>>(perm, n, dim * dim, static_cast<const T*>(b->B0), B0);
+    double* u = nullptr;
+    float* uhi = nullptr;
+    if (b->u) {
+        SRDR_TRY(dalloc(b, &u, (size_t)n * 4));
+        k_perm_rows<double><<<nb, kThreads, 0, st>>>(perm, n, 4, b->u, u);
+    } else {
+        SRDR_TRY(dalloc(b, &uhi, (size_t)n * 4));
+        k_perm_rows<float><<<nb, kThreads, 0, st>>>(perm, n, 4, b->uhi, uhi);
+    }
+    T* bf = nullptr;
+    if (b->bf) {
+        SRDR_TRY(dalloc(b, &bf, (size_t)n * 4));
+        k_perm_rows<T><<<nb, kThreads, 0, st>>>(perm, n, 4, static_cast<const T*>(b->bf), bf);
+    }
+    if (dim == 2)
+        k_stencil_gsum<T, 2><<<nb, kThreads, 0, st>>>(n, b->st_off, static_cast<const T*>(b->st_g), b->st_k,
+                                                      b->lat[0], b->lat[1], b->lat[2], static_cast<T*>(b->Gs));
+    else
+        k_stencil_gsum<T, 3><<<nb, kThreads, 0, st>>>(n, b->st_off, static_cast<const T*>(b->st_g), b->st_k,
+                                                      b->lat[0], b->lat[1], b->lat[2], static_cast<T*>(b->Gs));
+    if (b->foot_tab) {
+        int total = 0;
+        SRDR_CK(cudaMemcpyAsync(&total, b->foot_ptr + b->ncells, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SRDR_CK(cudaStreamSynchronize(st));
+        k_map_idx<<<nblocks(total), kThreads, 0, st>>>(perm, total, b->foot_tab);
+    }
+    SRDR_CK(cudaGetLastError());
+    SRDR_CK(cudaStreamSynchronize(st));
+    SRDR_TRY(dev_free(b, b->flags));
+    SRDR_TRY(dev_free(b, b->minv));
+    SRDR_TRY(dev_free(b, b->v));
+    SRDR_TRY(dev_free(b, b->B0));
+    SRDR_TRY(dev_free(b, b->u));
+    SRDR_TRY(dev_free(b, b->uhi));
+    SRDR_TRY(dev_free(b, b->bf));
+    b->mass_sw = b->mass;
+    b->flags = fl;
+    b->mass = m;
+    b->minv = mi;
+    b->v = v;
+    b->B0 = B0;
+    b->u = u;
+    b->uhi = uhi;
+    b->bf = bf;
+    b->pidx = b->perm;
+    b->stencil = 1;
+    b->pass_tiled = 0;
+    return SRDR_OK;
+}
+
 template <typename T>
 srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const double* vol_host,
                         const uint8_t* flags_host, const double* u0_host)
@@ -895,32 +1132,37 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
                                                       kcT, Gs);
     SRDR_CK(cudaGetLastError());
 
-    // sliced ELL for the passes
+    // the passes' neighbour enumeration: the lattice stencil (lattice bodies
+    // whose neighbour lists it reproduces), else the sliced ELL
     b->nslices = (n + 31) / 32;
+    bool stencil = false;
+    if (b->lat[0] > 0) SRDR_TRY(try_stencil<T>(b, vol_host ? vol_host[0] : b->vol0, &stencil));
     int* slots = nullptr;
-    SRDR_TRY(dalloc(b, &slots, b->nslices));
-    SRDR_TRY(dalloc(b, &b->sell_ptr, (size_t)b->nslices + 1));
-    k_sell_width<<<nblocks(b->nslices), kThreads, 0, st>>>(b->row_ptr, n, b->nslices, slots);
-    SRDR_TRY(scan_exclusive(slots, b->sell_ptr, b->nslices, tmp, st));
-    int nslots = 0;
-    SRDR_CK(cudaMemcpyAsync(&nslots, b->sell_ptr + b->nslices, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SRDR_CK(cudaStreamSynchronize(st));
-    if (nslots < 0) {
-        set_error("sliced-ELL layout exceeds 2^31 slots");
-        return SRDR_ERR_INVALID;
+    if (!stencil) {
+        SRDR_TRY(dalloc(b, &slots, b->nslices));
+        SRDR_TRY(dalloc(b, &b->sell_ptr, (size_t)b->nslices + 1));
+        k_sell_width<<<nblocks(b->nslices), kThreads, 0, st>>>(b->row_ptr, n, b->nslices, slots);
+        SRDR_TRY(scan_exclusive(slots, b->sell_ptr, b->nslices, tmp, st));
+        int nslots = 0;
+        SRDR_CK(cudaMemcpyAsync(&nslots, b->sell_ptr + b->nslices, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SRDR_CK(cudaStreamSynchronize(st));
+        if (nslots < 0) {
+            set_error("sliced-ELL layout exceeds 2^31 slots");
+            return SRDR_ERR_INVALID;
+        }
+        b->nslots = nslots;
+        const int64_t ns = std::max(nslots, 1);
+        SRDR_TRY(dalloc(b, &b->sell_col, ns));
+        T* sg = nullptr;
+        SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
+        b->sell_g = sg;
+        if (dim == 2)
+            k_sell_fill<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
+                                                               rcT, ihT, kcT, b->sell_col, sg, ns);
+        else
+            k_sell_fill<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
+                                                               rcT, ihT, kcT, b->sell_col, sg, ns);
     }
-    b->nslots = nslots;
-    const int64_t ns = std::max(nslots, 1);
-    SRDR_TRY(dalloc(b, &b->sell_col, ns));
-    T* sg = nullptr;
-    SRDR_TRY(dalloc(b, &sg, (size_t)ns * 3));
-    b->sell_g = sg;
-    if (dim == 2)
-        k_sell_fill<T, 2><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
-                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
-    else
-        k_sell_fill<T, 3><<<nblocks(n), kThreads, 0, st>>>(n, b->row_ptr, b->col, b->sell_ptr, cpos, b->ccell,
-                                                           rcT, ihT, kcT, b->sell_col, sg, ns);
 
     // footprint maxima size the damping sweep's shared memory
     int* fs = nullptr;
@@ -1024,6 +1266,7 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
             return SRDR_ERR_INVALID;
         }
     }
+    if (stencil) SRDR_TRY(relayout_stencil<T>(b));
     return SRDR_OK;
 }
 
@@ -1367,7 +1610,7 @@ srdr_status prepare_sweep_typed(srdr_body* b)
     }
     const T c = (T)(b->eta / b->desc.alpha * b->dt);
     k_sweep_consts<T><<<nblocks(b->n), kThreads, 0, b->stream>>>(
-        (int)b->n, c, static_cast<const T*>(b->mass), static_cast<const T*>(b->sumw),
+        (int)b->n, c, static_cast<const T*>(b->stencil ? b->mass_sw : b->mass), static_cast<const T*>(b->sumw),
         static_cast<const T*>(b->sumw2), static_cast<T*>(b->sbm), static_cast<T*>(b->srd));
     k_sweep_slots<T><<<nblocks(b->nnz + 2), kThreads, 0, b->stream>>>(
         b->nnz, c, static_cast<const T*>(b->w), b->loc, static_cast<SweepSlot<T>*>(b->srec));

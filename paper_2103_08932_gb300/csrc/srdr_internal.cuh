@@ -134,6 +134,10 @@ struct BrickInfo {
 // device error codes written to DevScalars::status
 enum { DEV_OK = 0, DEV_SINGULAR_B0 = 1, DEV_NONFINITE = 2, DEV_TIMEOUT = 3 };
 
+// neighbour slots per batch of loads in the passes; lattice-stencil tables
+// are padded to a multiple of it
+constexpr int kStencilBatch = 8;
+
 template <typename T>
 struct StepArgs {
     int n;
@@ -162,6 +166,16 @@ struct StepArgs {
     T rc, inv_h, kc;             // cell edge, 1/h, -5 alpha_d / h^2
     T grav[3];
     T endl[3];
+    // lattice stencil (bodies on a box lattice of lx x ly x lz points, x
+    // fastest, particle index = lattice index): neighbour k of particle i is
+    // i + st_off[k].w where the lattice point (x, y, z) + st_off[k].xyz lies
+    // in the box, with the pair gradient st_g[k] (T [st_k][4]); st_k is a
+    // multiple of the passes' batch, padded with zero offsets.  Null for the
+    // sliced-ELL and brick mappings.
+    const int4* __restrict__ st_off;
+    const T* __restrict__ st_g;
+    int st_k;
+    int lx, ly, lz;
 };
 
 // One slot of a damping-sweep row: B_j = c w_ij, pre-scaled by the body's
@@ -193,10 +207,14 @@ struct SweepArgs {
     const uint16_t* __restrict__ loc;
     const T* __restrict__ w;
     const SweepSlot<T>* __restrict__ rec;  // [nnz + 2] (B_j, footprint-local j) per row entry
-    const T* __restrict__ mass;
+    const T* __restrict__ mass;  // [n] sorted order
     const T* __restrict__ sbm;   // [n] sum_j B_j - m_i of the local solve (Sec. 3.1)
     const T* __restrict__ srd;   // [n] 1 / ((sum_j B_j - m_i)^2 + sum_j B_j^2)
-    T* __restrict__ v;
+    T* __restrict__ v;           // [n][4] particle order
+    // sorted index -> particle index when the particle arrays are not in
+    // sorted order (lattice-stencil bodies keep them in lattice order), else
+    // null; the 2^d layout's touched lists already hold particle indices
+    const int* __restrict__ pidx;
     DevScalars* sc;
     const int* dflag;  // device-decided damping of this step (graph replay), else null
     T c;          // 2 eta~ dt_loc, so that B_j = c w_ij
@@ -234,10 +252,23 @@ struct srdr_body {
     int* foot_tab = nullptr;
     int* own_off = nullptr;
     double lo[3] = {0, 0, 0};
+    // lattice stencil of the passes (bodies on a box lattice whose neighbour
+    // lists the stencil reproduces): the particle arrays are then in lattice
+    // (= original) order and pidx maps the sweep's sorted index to it
+    int stencil = 0;
+    int lat[3] = {0, 0, 0};     // lattice points per axis (0: not a lattice body)
+    int st_k = 0;               // offsets, padded to a multiple of the passes' batch
+    int4* st_off = nullptr;     // [st_k] (dx, dy, dz, index delta)
+    void* st_g = nullptr;       // T [st_k][4] pair gradient of each offset
+    int* pidx = nullptr;        // sorted -> particle index (= perm), stencil bodies only
+    void* mass_sw = nullptr;    // T [n] masses in sorted order (the sweep's), stencil bodies only
 
     // device arrays
     int* perm = nullptr;        // sorted -> original
     int* inv = nullptr;         // original -> sorted
+    // particle-array index -> original (perm, or null: the identity for
+    // lattice-stencil bodies, whose arrays are in original order)
+    const int* io_perm() const { return stencil ? nullptr : perm; }
     int* cell_start = nullptr;  // [ncells+1]
     int* cell_of = nullptr;     // [n] cell id, sorted order
     int* colour_cells = nullptr;

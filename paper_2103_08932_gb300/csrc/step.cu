@@ -72,10 +72,11 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     s.loc = b->loc;
     s.w = static_cast<const T*>(b->w);
     s.rec = static_cast<const SweepSlot<T>*>(b->srec);
-    s.mass = static_cast<const T*>(b->mass);
+    s.mass = static_cast<const T*>(b->stencil ? b->mass_sw : b->mass);
     s.sbm = static_cast<const T*>(b->sbm);
     s.srd = static_cast<const T*>(b->srd);
     s.v = static_cast<T*>(b->v);
+    s.pidx = b->pidx;
     s.sc = b->sc;
     // B_j = 2 eta~ V_i V_j W'/r dt_loc with eta~ = eta / alpha, dt_loc = dt / 2
     s.c = (T)(b->eta / b->desc.alpha * b->dt);
@@ -244,6 +245,10 @@ srdr_status autotune_sweep(srdr_body* b)
 template <typename T, int D, int MAT>
 srdr_status choose_pass_mapping(srdr_body* b)
 {
+    if (b->stencil) {
+        b->pass_tiled = 0;
+        return SRDR_OK;
+    }
     if (b->pass_mapping != SRDR_PASS_BRICKS) {
         b->pass_tiled = 0;
         return SRDR_OK;
@@ -322,8 +327,10 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         prof_begin(b, SRDR_K_PASS_A, &ev);
         if (tiled)
             k_pass_a_tiled<T, D, MAT><<<b->nbricks, kTileThreads, smem_a, q>>>(A, tl);
+        else if (b->stencil)
+            k_pass_a<T, D, MAT, 1><<<nb, kThreads, 0, q>>>(A);
         else
-            k_pass_a<T, D, MAT><<<nb, kThreads, 0, q>>>(A);
+            k_pass_a<T, D, MAT, 0><<<nb, kThreads, 0, q>>>(A);
         prof_end(b, SRDR_K_PASS_A, ev);
         counted(SRDR_K_PASS_A, 1);
         if (explicit_visc) {
@@ -331,16 +338,18 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
             prof_begin(b, SRDR_K_SWEEP, &ev);
             k_visc<T, D><<<nb, kThreads, 0, q>>>((int)b->n, b->row_ptr, b->col,
                                                  static_cast<const T*>(b->w), static_cast<const T*>(b->v),
-                                                 static_cast<const T*>(b->mass), c2eta_dt,
-                                                 static_cast<T*>(b->dvisc), b->sc);
+                                                 static_cast<const T*>(b->stencil ? b->mass_sw : b->mass),
+                                                 b->pidx, c2eta_dt, static_cast<T*>(b->dvisc), b->sc);
             prof_end(b, SRDR_K_SWEEP, ev);
             counted(SRDR_K_SWEEP, 1);
         }
         prof_begin(b, SRDR_K_PASS_B, &ev);
         if (tiled)
             k_pass_b_tiled<T, D><<<b->nbricks, kTileThreads, smem_b, q>>>(A, tl, damp ? 0 : 1);
+        else if (b->stencil)
+            k_pass_b<T, D, 1><<<nb, kThreads, 0, q>>>(A, damp ? 0 : 1);
         else
-            k_pass_b<T, D><<<nb, kThreads, 0, q>>>(A, damp ? 0 : 1);
+            k_pass_b<T, D, 0><<<nb, kThreads, 0, q>>>(A, damp ? 0 : 1);
         prof_end(b, SRDR_K_PASS_B, ev);
         counted(SRDR_K_PASS_B, 1);
         if (dev ? damping : damp) {

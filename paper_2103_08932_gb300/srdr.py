@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsrdr.so")
 SRDR_PASS_AUTO = 0
 SRDR_PASS_SELL = 1
 SRDR_PASS_BRICKS = 2
+SRDR_PASS_STENCIL = 3
+SRDR_PASS_LAYOUT_AUTO, SRDR_PASS_LAYOUT_SELL = 0, 1
 SRDR_SWEEP_AUTO = 0
 SRDR_SWEEP_BARRIER = 1
 SRDR_SWEEP_CELLS = 2
@@ -87,6 +89,7 @@ class srdr_body_desc(C.Structure):
         ("dt", C.c_double),
         ("twist", C.c_double * 4),
         ("sweep_layout", C.c_int),
+        ("pass_layout", C.c_int),
     ]
 
 
@@ -174,7 +177,7 @@ def _ptr(a):
 
 
 def make_desc(spec, precision=SRDR_FP64, damping=SRDR_DAMP_PARTICLE, dt=0.0,
-              sweep_layout=0) -> srdr_body_desc:
+              sweep_layout=0, pass_layout=0) -> srdr_body_desc:
     """C description from a synth.BodySpec-like object."""
     d = srdr_body_desc()
     d.dim = spec.dim
@@ -198,6 +201,7 @@ def make_desc(spec, precision=SRDR_FP64, damping=SRDR_DAMP_PARTICLE, dt=0.0,
     d.dt = dt
     d.twist = (C.c_double * 4)(*getattr(spec, "twist", (0.0, 0.0, 0.0, 0.0)))
     d.sweep_layout = sweep_layout
+    d.pass_layout = pass_layout
     return d
 
 
@@ -294,7 +298,8 @@ class Body:
         _check(lib().srdr_body_debug_stall_sweep(self.h))
 
     def pass_mapping(self, mapping=0, brick=(0, 0, 0)):
-        """SRDR_PASS_AUTO (0), SRDR_PASS_SELL (1) or SRDR_PASS_BRICKS (2),
+        """SRDR_PASS_AUTO (0), SRDR_PASS_SELL (1), SRDR_PASS_BRICKS (2) or
+        SRDR_PASS_STENCIL (3, lattice-stencil bodies only),
         with the brick size in cells (0 = default)."""
         bx, by, bz = (int(x) for x in brick)
         _check(lib().srdr_body_pass_mapping(self.h, int(mapping), bx, by, bz))

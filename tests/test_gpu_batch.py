@@ -45,6 +45,12 @@ def uneven_specs(dim=3):
 MODES = [srdr.SRDR_BATCH_SHARED, srdr.SRDR_BATCH_STREAMS]
 
 
+def layout_for(mode):
+    """Shared launches take sliced-ELL bodies; concurrent streams take any
+    body (the lattice bodies here take the stencil)."""
+    return srdr.SRDR_PASS_LAYOUT_SELL if mode == srdr.SRDR_BATCH_SHARED else srdr.SRDR_PASS_LAYOUT_AUTO
+
+
 @pytest.mark.parametrize("mode", MODES, ids=["shared", "streams"])
 @pytest.mark.parametrize("dim,precision,sync", [
     (3, srdr.SRDR_FP64, srdr.SRDR_SWEEP_AUTO), (3, srdr.SRDR_FP32_MIXED, srdr.SRDR_SWEEP_AUTO),
@@ -56,11 +62,12 @@ def test_batch_steps_equal_single_bodies(dim, precision, sync, mode):
     alone (cell-wise or barrier single-body sweep) bit for bit; the bodies
     then keep stepping alone and still agree."""
     specs = uneven_specs(dim)
-    single = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
+    lay = layout_for(mode)
+    single = [srdr.Body(srdr.make_desc(s, precision=precision, pass_layout=lay)) for s in specs]
     for b in single:
         b.sweep_sync(srdr.SRDR_SWEEP_BARRIER if sync == srdr.SRDR_SWEEP_CELLS else srdr.SRDR_SWEEP_CELLS)
         b.step(40)
-    bodies = [srdr.Body(srdr.make_desc(s, precision=precision)) for s in specs]
+    bodies = [srdr.Body(srdr.make_desc(s, precision=precision, pass_layout=lay)) for s in specs]
     for b in bodies:
         b.sweep_sync(sync)
     batch = srdr.Batch(bodies)
@@ -85,12 +92,13 @@ def test_batch_relax_retires_each_body_at_its_own_step(mode):
     specs = uneven_specs(3)
     tol = 1e-6
     single_steps, single_u = [], []
+    lay = layout_for(mode)
     for s in specs:
-        b = srdr.Body(srdr.make_desc(s))
+        b = srdr.Body(srdr.make_desc(s, pass_layout=lay))
         status, steps, ratio = b.relax(tol, 200000)
         single_steps.append(steps)
         single_u.append(b.displacement())
-    bodies = [srdr.Body(srdr.make_desc(s)) for s in specs]
+    bodies = [srdr.Body(srdr.make_desc(s, pass_layout=lay)) for s in specs]
     batch = srdr.Batch(bodies)
     batch.mode(mode)
     status, st, steps = batch.run(tol, 200000)
@@ -117,7 +125,7 @@ def test_batch_relax_one_call():
 @pytest.mark.parametrize("mode", MODES, ids=["shared", "streams"])
 def test_batch_step_cap_reports_not_converged(mode):
     specs = uneven_specs(3)[:1]
-    bodies = [srdr.Body(srdr.make_desc(s)) for s in specs]
+    bodies = [srdr.Body(srdr.make_desc(s, pass_layout=layout_for(mode))) for s in specs]
     batch = srdr.Batch(bodies)
     batch.mode(mode)
     status, st, steps = batch.run(1e-12, 50)
@@ -179,3 +187,23 @@ def test_batch_mode_rejects_unknown():
     with pytest.raises(srdr.SrdrError) as e:
         batch.mode(5)
     assert e.value.status == srdr.SRDR_ERR_INVALID
+
+
+def test_shared_launches_take_sliced_ell_bodies_only():
+    """A batch holding a lattice-stencil body refuses shared launches and
+    keeps its mode; the same bodies created with the sliced ELL accept them."""
+    spec = uneven_specs(3)[0]
+    st = srdr.Body(srdr.make_desc(spec))
+    assert st.stats()["pass_mapping"] == srdr.SRDR_PASS_STENCIL
+    batch = srdr.Batch([st])
+    with pytest.raises(srdr.SrdrError) as e:
+        batch.mode(srdr.SRDR_BATCH_SHARED)
+    assert e.value.status == srdr.SRDR_ERR_INVALID and "sliced-ELL" in srdr.last_error()
+    batch.mode(srdr.SRDR_BATCH_STREAMS)
+    batch.step(3)
+    batch.close()
+    sell = srdr.Body(srdr.make_desc(spec, pass_layout=srdr.SRDR_PASS_LAYOUT_SELL))
+    batch = srdr.Batch([sell])
+    batch.mode(srdr.SRDR_BATCH_SHARED)
+    batch.step(3)
+    batch.close()

@@ -42,8 +42,9 @@ def oracle_for(spec, parts=None, damping=O.DAMP_PARTICLE, layout=O.SWEEP_2D):
     return O.OracleBody(p, r0[:, :spec.dim], vol_default=spec.vol, flags=flags)
 
 
-def gpu_for(spec, parts=None, precision=srdr.SRDR_FP64, damping=srdr.SRDR_DAMP_PARTICLE, layout=L2D):
-    d = srdr.make_desc(spec, precision=precision, damping=damping, sweep_layout=layout)
+def gpu_for(spec, parts=None, precision=srdr.SRDR_FP64, damping=srdr.SRDR_DAMP_PARTICLE, layout=L2D,
+            pass_layout=srdr.SRDR_PASS_LAYOUT_AUTO):
+    d = srdr.make_desc(spec, precision=precision, damping=damping, sweep_layout=layout, pass_layout=pass_layout)
     if parts is None:
         return srdr.Body(d)
     r0, flags, u0 = parts
@@ -140,7 +141,7 @@ def test_layout_changes_only_the_sweep():
 
 
 def test_layout_refused_by_batches_and_bricks():
-    a = gpu_for(B3)
+    a = gpu_for(B3, pass_layout=srdr.SRDR_PASS_LAYOUT_SELL)
     with pytest.raises(srdr.SrdrError) as e:
         srdr.Batch([a])
     assert e.value.status == srdr.SRDR_ERR_INVALID

@@ -40,8 +40,8 @@ def oracle_for(spec, r0=None, flags=None, u0=None, damping=O.DAMP_PARTICLE, dt=0
 
 
 def gpu_for(spec, precision=srdr.SRDR_FP64, damping=srdr.SRDR_DAMP_PARTICLE, particles=None,
-            dt=0.0):
-    d = srdr.make_desc(spec, precision=precision, damping=damping, dt=dt)
+            dt=0.0, pass_layout=srdr.SRDR_PASS_LAYOUT_AUTO):
+    d = srdr.make_desc(spec, precision=precision, damping=damping, dt=dt, pass_layout=pass_layout)
     if particles is None:
         return srdr.Body(d)
     r0, flags, u0 = particles
@@ -425,14 +425,15 @@ def test_pass_mappings_are_bitwise_equal(spec, precision, jit):
     velocities and kinetic energies agree bit for bit, on damped and undamped
     steps."""
     parts = S.jittered(spec, 0.3, 5) if jit else None
-    ref = gpu_for(spec, precision=precision, particles=parts)
+    sell = srdr.SRDR_PASS_LAYOUT_SELL
+    ref = gpu_for(spec, precision=precision, particles=parts, pass_layout=sell)
     ref.pass_mapping(srdr.SRDR_PASS_SELL)
     ref.step(14)
     assert ref.stats()["pass_mapping"] == srdr.SRDR_PASS_SELL
     assert 0 < ref.stats()["damped_steps"] < 14
     bricks = [(0, 0, 0), (1, 1, 1), (3, 2, 1), (4, 4, 4)]
     for brick in bricks:
-        b = gpu_for(spec, precision=precision, particles=parts)
+        b = gpu_for(spec, precision=precision, particles=parts, pass_layout=sell)
         b.pass_mapping(srdr.SRDR_PASS_BRICKS, brick)
         b.step(14)
         st = b.stats()
@@ -440,7 +441,7 @@ def test_pass_mappings_are_bitwise_equal(spec, precision, jit):
         assert np.array_equal(b.displacement(), ref.displacement()), brick
         assert np.array_equal(b.velocity(), ref.velocity()), brick
         assert st["ke"] == ref.stats()["ke"] and st["ke_max"] == ref.stats()["ke_max"], brick
-    auto = gpu_for(spec, precision=precision, particles=parts)
+    auto = gpu_for(spec, precision=precision, particles=parts, pass_layout=sell)
     auto.step(14)
     assert auto.stats()["pass_mapping"] in (srdr.SRDR_PASS_SELL, srdr.SRDR_PASS_BRICKS)
     assert np.array_equal(auto.velocity(), ref.velocity())
@@ -451,7 +452,7 @@ def test_brick_mapping_matches_oracle_fp64():
     steps, FP64), besides their bitwise equality with the sliced-ELL passes."""
     spec = S.cantilever_2d(S.NEO_HOOKEAN)
     ob = oracle_for(spec)
-    gb = gpu_for(spec)
+    gb = gpu_for(spec, pass_layout=srdr.SRDR_PASS_LAYOUT_SELL)
     gb.pass_mapping(srdr.SRDR_PASS_BRICKS, (2, 2, 1))
     ob.step(30)
     gb.step(30)
@@ -461,11 +462,63 @@ def test_brick_mapping_matches_oracle_fp64():
 
 
 def test_pass_mapping_rejects_bad_arguments():
-    b = gpu_for(SMALL3D)
-    for args in ((3, (0, 0, 0)), (-1, (0, 0, 0)), (2, (5, 1, 1)), (2, (1, -1, 1))):
+    b = gpu_for(SMALL3D, pass_layout=srdr.SRDR_PASS_LAYOUT_SELL)
+    for args in ((4, (0, 0, 0)), (-1, (0, 0, 0)), (2, (5, 1, 1)), (2, (1, -1, 1)),
+                 (srdr.SRDR_PASS_STENCIL, (0, 0, 0))):
         with pytest.raises(srdr.SrdrError) as e:
             b.pass_mapping(*args)
         assert e.value.status == srdr.SRDR_ERR_INVALID
+    # a lattice-stencil body keeps its mapping: the other two are refused
+    st = gpu_for(SMALL3D)
+    st.pass_mapping(srdr.SRDR_PASS_STENCIL)
+    st.pass_mapping(srdr.SRDR_PASS_AUTO)
+    for m in (srdr.SRDR_PASS_SELL, srdr.SRDR_PASS_BRICKS):
+        with pytest.raises(srdr.SrdrError) as e:
+            st.pass_mapping(m)
+        assert e.value.status == srdr.SRDR_ERR_INVALID
+    with pytest.raises(srdr.SrdrError) as e:
+        srdr.Body(srdr.make_desc(SMALL3D, pass_layout=5))
+    assert e.value.status == srdr.SRDR_ERR_INVALID
+
+
+# ------------------------------------------------------------------ lattice stencil
+@pytest.mark.parametrize("spec", [SMALL2D, SMALL3D, S.cantilever_2d(S.NEO_HOOKEAN)])
+def test_lattice_bodies_take_the_stencil(spec):
+    """Lattice bodies, built by the library or passed as explicit particles
+    in lattice order, take the stencil mapping; a jittered particle set or
+    pass_layout = SELL keeps the sliced ELL."""
+    for body in (gpu_for(spec), gpu_for(spec, particles=S.lattice(spec))):
+        body.step(2)
+        assert body.stats()["pass_mapping"] == srdr.SRDR_PASS_STENCIL
+    jit = gpu_for(spec, particles=S.jittered(spec, 0.3, 5))
+    jit.step(2)
+    assert jit.stats()["pass_mapping"] == srdr.SRDR_PASS_SELL
+    sell = gpu_for(spec, pass_layout=srdr.SRDR_PASS_LAYOUT_SELL)
+    sell.step(2)
+    assert sell.stats()["pass_mapping"] == srdr.SRDR_PASS_SELL
+
+
+@pytest.mark.parametrize("spec,precision,tol", [
+    (SMALL3D, srdr.SRDR_FP64, 1e-12), (SMALL2D, srdr.SRDR_FP64, 1e-12),
+    (SMALL3D, srdr.SRDR_FP32_MIXED, 1e-5), (SMALL2D, srdr.SRDR_FP32_MIXED, 1e-5)])
+def test_stencil_matches_sliced_ell(spec, precision, tol):
+    """The same body with the lattice stencil and with the sliced ELL over 40
+    steps (damped and undamped): the stencil's pair gradients are evaluated
+    once per lattice offset from the exact offset, the sliced ELL's once per
+    pair from the positions, so the two agree to rounding: the FP64 tolerance
+    is a few thousand ulps, the FP32 one the FP32-mixed bar."""
+    a = gpu_for(spec, precision=precision)
+    b = gpu_for(spec, precision=precision, pass_layout=srdr.SRDR_PASS_LAYOUT_SELL)
+    worst_v = worst_u = 0.0
+    for _ in range(40):
+        a.step(1)
+        b.step(1)
+        worst_v = max(worst_v, rel(a.velocity(), b.velocity()))
+        worst_u = max(worst_u, rel(a.displacement(), b.displacement()))
+    assert a.stats()["damped_steps"] == b.stats()["damped_steps"] > 0
+    assert worst_v <= tol and worst_u <= tol, (worst_v, worst_u)
+    # the correction matrices are the same set-up result, read in original order
+    assert np.array_equal(a.field(srdr.SRDR_FIELD_B0), b.field(srdr.SRDR_FIELD_B0))
 
 
 # ------------------------------------------------------------------ explicit comparator
