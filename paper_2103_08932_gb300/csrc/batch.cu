@@ -396,8 +396,7 @@ SweepArgs<T> sweep_args(srdr_body* b, int F, int P, int C)
     s.mass = static_cast<const T*>(b->stencil ? b->mass_sw : b->mass);
     s.sbm = static_cast<const T*>(b->sbm);
     s.srd = static_cast<const T*>(b->srd);
-    s.v = static_cast<T*>(b->v);
-    s.pidx = b->pidx;
+    s.v = static_cast<T*>(b->stencil ? b->vs : b->v);
     s.sc = b->sc;
     s.c = b->desc.alpha > 0 ? (T)(b->eta / b->desc.alpha * b->dt) : T(0);
     s.pairwise = b->desc.damping == SRDR_DAMP_PAIRWISE;

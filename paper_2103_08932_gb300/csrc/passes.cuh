@@ -398,6 +398,57 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(StepArgs<T> a)
         pass_a_particle<T, D, MAT>(a, i);
 }
 
+// The stress pass with the stencil table as a kernel parameter: K offsets,
+// the loop fully unrolled so that every table read is a constant-bank load at
+// a fixed offset (the same for the whole warp), leaving the L1 path to the
+// neighbour gathers.  Same table values in the same order as the global
+// table above, so the same bits.
+template <typename T, int D, int K>
+__device__ inline void stencil_slots_tab(const StencilTab<T, K>& tb, const StepArgs<T>& a, int i, int x, int y,
+                                         int z, int k0, int (&jj)[kUnroll], T (&gg)[kUnroll][D])
+{
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int k = k0 + u;
+        const bool in = (unsigned)(x + tb.dx[k]) < (unsigned)a.lx && (unsigned)(y + tb.dy[k]) < (unsigned)a.ly &&
+                        (unsigned)(z + tb.dz[k]) < (unsigned)a.lz;
+        jj[u] = in ? i + tb.delta[k] : i;
+        gg[u][0] = tb.g[k][0];
+        gg[u][1] = tb.g[k][1];
+        if constexpr (D == 3) gg[u][2] = tb.g[k][2];
+    }
+}
+
+template <typename T, int D, int MAT, int K>
+__global__ void __launch_bounds__(kThreads) k_pass_a_tab(StepArgs<T> a, const __grid_constant__ StencilTab<T, K> tb)
+{
+    static_assert(K % kUnroll == 0, "stencil tables are padded to the passes' batch");
+    if (a.sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int x, y, z;
+    lattice_xyz(i, a.lx, a.ly, x, y, z);
+    T xi[3], li[3];
+    UAcc<T>::load(a.u, a.uhi, a.ulo, i, xi, li);
+    T G[D][D];
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+        for (int q = 0; q < D; ++q) G[p][q] = 0;
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
+        stencil_slots_tab<T, D, K>(tb, a, i, x, y, z, k0, jj, gg);
+        T xj[kUnroll][3], lj[kUnroll][3];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) UAcc<T>::load(a.u, a.uhi, a.ulo, jj[u], xj[u], lj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) acc_grad<T, D>(G, xi, li, xj[u], lj[u], gg[u]);
+    }
+    pass_a_epilogue<T, D, MAT>(a, i, G);
+}
+
 // ------------------------------------------------------------------ reductions
 __device__ inline double warp_sum(double x)
 {
@@ -620,7 +671,11 @@ __device__ inline double pass_b_epilogue(const StepArgs<T>& a, int i, T (&acc)[D
     v4.x = vi[0];
     v4.y = vi[1];
     v4.z = vi[2];
-    st_v4<T>(a.v, i, v4);
+    // a damped step of a stencil body: v* goes to the sweep's sorted copy
+    if (a.vs && !final_step)
+        st_v4<T>(a.vs, __ldg(a.inv + i), v4);
+    else
+        st_v4<T>(a.v, i, v4);
     if (final_step && !(f & SRDR_FLAG_CONSTRAINED)) {
         T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
         u_add<T>(a, i, d);
@@ -684,6 +739,41 @@ __device__ inline double pass_b_particle_st(const StepArgs<T>& a, int i, int fin
     return pass_b_epilogue<T, D>(a, i, acc, Pi, final_step);
 }
 
+// the force pass with the stencil table as a kernel parameter (see
+// k_pass_a_tab)
+template <typename T, int D, int K>
+__global__ void __launch_bounds__(kThreads, 3) k_pass_b_tab(StepArgs<T> a, const __grid_constant__ StencilTab<T, K> tb,
+                                                           int final_step)
+{
+    static_assert(K % kUnroll == 0, "stencil tables are padded to the passes' batch");
+    if (a.sc->done) return;
+    if (a.dflag) final_step = *a.dflag == 0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    if (i < a.n) {
+        int x, y, z;
+        lattice_xyz(i, a.lx, a.ly, x, y, z);
+        T Pi[D][D];
+        PBL<T, D>::load(a.PB, a.n, i, Pi);
+        T acc[D];
+#pragma unroll
+        for (int p = 0; p < D; ++p) acc[p] = 0;
+#pragma unroll
+        for (int k0 = 0; k0 < K; k0 += kUnroll) {
+            int jj[kUnroll];
+            T gg[kUnroll][D];
+            stencil_slots_tab<T, D, K>(tb, a, i, x, y, z, k0, jj, gg);
+            T Pj[kUnroll][D][D];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, a.n, jj[u], Pj[u]);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) acc_force<T, D>(acc, Pi, Pj[u], gg[u]);
+        }
+        ke = pass_b_epilogue<T, D>(a, i, acc, Pi, final_step);
+    }
+    if (final_step) ke_last_block(a, ke, 0);
+}
+
 template <typename T, int D, int ST>
 __global__ void __launch_bounds__(kThreads, 3) k_pass_b(StepArgs<T> a, int final_step)
 {
@@ -708,11 +798,14 @@ __device__ inline double finish_particle(const StepArgs<T>& a, int i)
     double ke = 0.0;
     {
         uint8_t f = a.flags[i];
-        vec4_t<T> v4 = ld_v4<T>(a.v, i);
+        // a stencil body's damped velocities come from the sweep's sorted
+        // copy and go back to v
+        vec4_t<T> v4 = a.vs ? ld_v4<T>(a.vs, __ldg(a.inv + i)) : ld_v4<T>(a.v, i);
         if (f & SRDR_FLAG_CONSTRAINED) {
             v4.x = v4.y = v4.z = 0;
             st_v4<T>(a.v, i, v4);
         } else {
+            if (a.vs) st_v4<T>(a.v, i, v4);
             const T vi[3] = {v4.x, v4.y, v4.z};
             T d[3] = {a.dt * vi[0], a.dt * vi[1], a.dt * vi[2]};
             u_add<T>(a, i, d);
@@ -827,6 +920,25 @@ StepArgs<T> make_step_args(srdr_body* b)
         a.lx = b->lat[0];
         a.ly = b->lat[1];
         a.lz = b->lat[2];
+        a.vs = static_cast<T*>(b->vs);
+        a.inv = b->inv;
     }
     return a;
+}
+
+// the body's stencil as a kernel-parameter table of K offsets (the same
+// values, rounded to T once, as its device table)
+template <typename T, int K>
+StencilTab<T, K> make_stencil_tab(const srdr_body* b)
+{
+    StencilTab<T, K> t{};
+    for (int k = 0; k < K && k < (int)b->st_off_h.size(); ++k) {
+        const int4 o = b->st_off_h[k];
+        t.delta[k] = o.w;
+        t.dx[k] = o.x;
+        t.dy[k] = o.y;
+        t.dz[k] = o.z;
+        for (int c = 0; c < 3; ++c) t.g[k][c] = (T)b->st_g_h[(size_t)k * 4 + c];
+    }
+    return t;
 }

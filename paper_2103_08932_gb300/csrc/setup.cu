@@ -773,7 +773,7 @@ __global__ void k_stencil_gsum(int n, const int4* __restrict__ off, const T* __r
 }
 
 // sorted -> particle order: rows of w elements (dst row perm[s] = src row s)
-// and columns of an [m][n] array; index lists mapped through perm
+// and columns of an [m][n] array
 template <typename E>
 __global__ void k_perm_rows(const int* __restrict__ perm, int n, int w, const E* __restrict__ src,
                             E* __restrict__ dst)
@@ -792,12 +792,6 @@ __global__ void k_perm_cols(const int* __restrict__ perm, int n, int m, const E*
     if (s >= n) return;
     const int i = perm[s];
     for (int c = 0; c < m; ++c) dst[(size_t)c * n + i] = src[(size_t)c * n + s];
-}
-
-__global__ void k_map_idx(const int* __restrict__ perm, int count, int* __restrict__ a)
-{
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < count) a[q] = perm[a[q]];
 }
 
 // The stencil of a lattice body (b->lat set by the create path): every
@@ -833,6 +827,7 @@ srdr_status try_stencil(srdr_body* b, double vol, bool* ok)
     if (K == 0 || K > 4096) return SRDR_OK;
     std::vector<int4> ho(K, int4{0, 0, 0, 0});
     std::vector<T> hg((size_t)K * 4, T(0));
+    std::vector<double> hgd((size_t)K * 4, 0.0);
     const double kc = kernel_kc(dim, b->h);
     for (size_t t = 0; t < offs.size(); ++t) {
         const Off& o = offs[t];
@@ -842,9 +837,10 @@ srdr_status try_stencil(srdr_body* b, double vol, bool* ok)
         const double r = std::sqrt(rx * rx + ry * ry + rz * rz);
         const double tt = std::max(1.0 - 0.5 * r / b->h, 0.0);
         const double w = kc * tt * tt * tt * vol;
-        hg[t * 4 + 0] = (T)(w * rx);
-        hg[t * 4 + 1] = (T)(w * ry);
-        hg[t * 4 + 2] = (T)(dim == 3 ? w * rz : 0.0);
+        hgd[t * 4 + 0] = w * rx;
+        hgd[t * 4 + 1] = w * ry;
+        hgd[t * 4 + 2] = dim == 3 ? w * rz : 0.0;
+        for (int c = 0; c < 3; ++c) hg[t * 4 + c] = (T)hgd[t * 4 + c];
     }
     int4* doff = nullptr;
     T* dg = nullptr;
@@ -870,16 +866,17 @@ srdr_status try_stencil(srdr_body* b, double vol, bool* ok)
     b->st_off = doff;
     b->st_g = dg;
     b->st_k = K;
+    b->st_off_h = ho;
+    b->st_g_h = hgd;
     *ok = true;
     return SRDR_OK;
 }
 
 // Move the particle arrays of a stencil body from sorted to lattice (=
-// original) order: flags, masses (the sorted copy stays for the sweep),
-// 1/m, u, v, B0, body force, and G_i from the stencil; the 2^d layout's
-// touched lists become particle indices.  The sweep's structures (cells,
-// rows, slot records) stay in sorted order and reach the particle arrays
-// through pidx = perm.
+// original) order: flags, masses, 1/m, u, v, B0, body force, and G_i from
+// the stencil.  The sweep keeps its structures (cells, rows, slot records)
+// and sorted copies of the masses and velocity records; pidx = perm maps
+// its sorted index to the particle arrays (the explicit comparator's rows).
 template <typename T>
 srdr_status relayout_stencil(srdr_body* b)
 {
@@ -918,22 +915,16 @@ srdr_status relayout_stencil(srdr_body* b)
     else
         k_stencil_gsum<T, 3><<<nb, kThreads, 0, st>>>(n, b->st_off, static_cast<const T*>(b->st_g), b->st_k,
                                                       b->lat[0], b->lat[1], b->lat[2], static_cast<T*>(b->Gs));
-    if (b->foot_tab) {
-        int total = 0;
-        SRDR_CK(cudaMemcpyAsync(&total, b->foot_ptr + b->ncells, sizeof(int), cudaMemcpyDeviceToHost, st));
-        SRDR_CK(cudaStreamSynchronize(st));
-        k_map_idx<<<nblocks(total), kThreads, 0, st>>>(perm, total, b->foot_tab);
-    }
     SRDR_CK(cudaGetLastError());
     SRDR_CK(cudaStreamSynchronize(st));
     SRDR_TRY(dev_free(b, b->flags));
     SRDR_TRY(dev_free(b, b->minv));
-    SRDR_TRY(dev_free(b, b->v));
     SRDR_TRY(dev_free(b, b->B0));
     SRDR_TRY(dev_free(b, b->u));
     SRDR_TRY(dev_free(b, b->uhi));
     SRDR_TRY(dev_free(b, b->bf));
     b->mass_sw = b->mass;
+    b->vs = b->v;  // the sorted records become the sweep's copy
     b->flags = fl;
     b->mass = m;
     b->minv = mi;

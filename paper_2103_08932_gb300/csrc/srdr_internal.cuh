@@ -138,6 +138,18 @@ enum { DEV_OK = 0, DEV_SINGULAR_B0 = 1, DEV_NONFINITE = 2, DEV_TIMEOUT = 3 };
 // are padded to a multiple of it
 constexpr int kStencilBatch = 8;
 
+// The lattice stencil as a kernel parameter (constant bank), for the usual
+// offset counts: K offsets with their index delta, lattice step and pair
+// gradient.  K = 80 in 3D and 24 in 2D for h = 1.3 dp (20 offsets padded).
+template <typename T, int K>
+struct StencilTab {
+    int delta[K];
+    int dx[K], dy[K], dz[K];
+    T g[K][3];
+};
+constexpr int kStencilK3 = 80;
+constexpr int kStencilK2 = 24;
+
 template <typename T>
 struct StepArgs {
     int n;
@@ -176,6 +188,12 @@ struct StepArgs {
     const T* __restrict__ st_g;
     int st_k;
     int lx, ly, lz;
+    // stencil bodies: the damping sweep's copy of the velocity records in
+    // sorted order (T [n][4]) and particle -> sorted index.  The force pass
+    // of a damped step writes v* there, the sweep works on it, and the
+    // finish pass copies the damped velocities back to v.  Null otherwise.
+    T* __restrict__ vs;
+    const int* __restrict__ inv;
 };
 
 // One slot of a damping-sweep row: B_j = c w_ij, pre-scaled by the body's
@@ -210,11 +228,7 @@ struct SweepArgs {
     const T* __restrict__ mass;  // [n] sorted order
     const T* __restrict__ sbm;   // [n] sum_j B_j - m_i of the local solve (Sec. 3.1)
     const T* __restrict__ srd;   // [n] 1 / ((sum_j B_j - m_i)^2 + sum_j B_j^2)
-    T* __restrict__ v;           // [n][4] particle order
-    // sorted index -> particle index when the particle arrays are not in
-    // sorted order (lattice-stencil bodies keep them in lattice order), else
-    // null; the 2^d layout's touched lists already hold particle indices
-    const int* __restrict__ pidx;
+    T* __restrict__ v;           // [n][4] sorted order (a stencil body's sorted copy)
     DevScalars* sc;
     const int* dflag;  // device-decided damping of this step (graph replay), else null
     T c;          // 2 eta~ dt_loc, so that B_j = c w_ij
@@ -254,14 +268,18 @@ struct srdr_body {
     double lo[3] = {0, 0, 0};
     // lattice stencil of the passes (bodies on a box lattice whose neighbour
     // lists the stencil reproduces): the particle arrays are then in lattice
-    // (= original) order and pidx maps the sweep's sorted index to it
+    // (= original) order; the sweep keeps sorted-order copies of the masses
+    // and velocity records
     int stencil = 0;
     int lat[3] = {0, 0, 0};     // lattice points per axis (0: not a lattice body)
     int st_k = 0;               // offsets, padded to a multiple of the passes' batch
     int4* st_off = nullptr;     // [st_k] (dx, dy, dz, index delta)
     void* st_g = nullptr;       // T [st_k][4] pair gradient of each offset
+    std::vector<int4> st_off_h;    // host copies of the table (kernel-parameter tables)
+    std::vector<double> st_g_h;    // [st_k][4], the values st_g holds before rounding to T
     int* pidx = nullptr;        // sorted -> particle index (= perm), stencil bodies only
     void* mass_sw = nullptr;    // T [n] masses in sorted order (the sweep's), stencil bodies only
+    void* vs = nullptr;         // T [n][4] velocity records in sorted order (the sweep's), stencil bodies only
 
     // device arrays
     int* perm = nullptr;        // sorted -> original

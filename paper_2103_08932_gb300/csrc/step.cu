@@ -75,8 +75,7 @@ SweepArgs<T> make_sweep_args(srdr_body* b)
     s.mass = static_cast<const T*>(b->stencil ? b->mass_sw : b->mass);
     s.sbm = static_cast<const T*>(b->sbm);
     s.srd = static_cast<const T*>(b->srd);
-    s.v = static_cast<T*>(b->v);
-    s.pidx = b->pidx;
+    s.v = static_cast<T*>(b->stencil ? b->vs : b->v);
     s.sc = b->sc;
     // B_j = 2 eta~ V_i V_j W'/r dt_loc with eta~ = eta / alpha, dt_loc = dt / 2
     s.c = (T)(b->eta / b->desc.alpha * b->dt);
@@ -295,6 +294,11 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
     void* sweep_params[] = {&sw, &cptr, &ncol, &bar};
     if (b->pass_tiled < 0) SRDR_TRY((choose_pass_mapping<T, D, MAT>(b)));
     const bool tiled = b->pass_tiled == 1;
+    // stencil bodies with the usual offset count take the table as a kernel
+    // parameter, the others read it from global memory
+    constexpr int KD = D == 3 ? kStencilK3 : kStencilK2;
+    const bool tab = b->stencil && b->st_k == KD;
+    const StencilTab<T, KD> stab = tab ? make_stencil_tab<T, KD>(b) : StencilTab<T, KD>{};
     TileArgs<T> tl{};
     size_t smem_a = 0, smem_b = 0;
     if (tiled) {
@@ -327,6 +331,8 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         prof_begin(b, SRDR_K_PASS_A, &ev);
         if (tiled)
             k_pass_a_tiled<T, D, MAT><<<b->nbricks, kTileThreads, smem_a, q>>>(A, tl);
+        else if (tab)
+            k_pass_a_tab<T, D, MAT, KD><<<nb, kThreads, 0, q>>>(A, stab);
         else if (b->stencil)
             k_pass_a<T, D, MAT, 1><<<nb, kThreads, 0, q>>>(A);
         else
@@ -346,6 +352,8 @@ srdr_status steps_typed(srdr_body* b, int64_t nsteps)
         prof_begin(b, SRDR_K_PASS_B, &ev);
         if (tiled)
             k_pass_b_tiled<T, D><<<b->nbricks, kTileThreads, smem_b, q>>>(A, tl, damp ? 0 : 1);
+        else if (tab)
+            k_pass_b_tab<T, D, KD><<<nb, kThreads, 0, q>>>(A, stab, damp ? 0 : 1);
         else if (b->stencil)
             k_pass_b<T, D, 1><<<nb, kThreads, 0, q>>>(A, damp ? 0 : 1);
         else

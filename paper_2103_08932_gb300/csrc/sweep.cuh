@@ -283,18 +283,13 @@ __device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellS
         const int rb = p0 & ~(R - 1);
         for (int k = rb + gl * R; k < p1; k += L * R) cp_async16s(s.srec + (k - rb), a.rec + k);
     }
-    // footprint-local index -> particle index (the 3^d neighbour cells'
-    // runs of sorted indices, mapped through pidx when the particle arrays
-    // are not in sorted order; the 2^d layout's list is being copied above)
+    // footprint-local index -> sorted particle index (the 3^d neighbour
+    // cells' runs; the 2^d layout's list is being copied above)
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         if (r < st.fr.nruns) {
             const int o = st.fr.off[r], len = st.fr.off[r + 1] - o, a0 = st.fr.a[r];
-            if (a.pidx) {
-                for (int q = gl; q < len; q += L) cp_async4(s.sfoot + o + q, a.pidx + a0 + q);
-            } else {
-                for (int q = gl; q < len; q += L) s.sfoot[o + q] = a0 + q;
-            }
+            for (int q = gl; q < len; q += L) s.sfoot[o + q] = a0 + q;
         }
     }
     for (int p = gl; p <= np; p += L) cp_async4(s.srow + p, a.row_ptr + st.cs + p);
@@ -324,7 +319,7 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
     const SweepSlot<T>* rec =
         a.rows_global ? a.rec + p0 : s.srec + (p0 & (16 / (int)sizeof(SweepSlot<T>) - 1));
     const int* sfoot = s.sfoot;
-    if (a.foot_tab || a.pidx) cp_async_wait_all();  // the footprint table arrives by cp.async
+    if (a.foot_tab) cp_async_wait_all();  // the touched list arrives by cp.async
     __syncwarp(gmask);  // the footprint table written by other lanes of the group
 
     // velocity records from L2 straight into shared memory

@@ -5,6 +5,8 @@ bit-exact.  Floating point: FP64 mode within 1e-9 relative after a few steps;
 both modes within the stated 1e-5 relative per-step velocity error over 100
 steps (max_i |v_gpu - v_oracle| / max_i |v_oracle| at every step).
 """
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -498,9 +500,17 @@ def test_lattice_bodies_take_the_stencil(spec):
     assert sell.stats()["pass_mapping"] == srdr.SRDR_PASS_SELL
 
 
+# h = 1.5 dp (3D, 92 offsets) and 1.6 dp (2D, 36 offsets) give offset counts
+# other than the usual 80 (3D) and 20 (2D): those bodies read the stencil
+# table from global memory instead of taking it as a kernel parameter
+WIDE3D = replace(SMALL3D, h_over_dp=1.5)
+WIDE2D = replace(SMALL2D, h_over_dp=1.6)
+
+
 @pytest.mark.parametrize("spec,precision,tol", [
     (SMALL3D, srdr.SRDR_FP64, 1e-12), (SMALL2D, srdr.SRDR_FP64, 1e-12),
-    (SMALL3D, srdr.SRDR_FP32_MIXED, 1e-5), (SMALL2D, srdr.SRDR_FP32_MIXED, 1e-5)])
+    (SMALL3D, srdr.SRDR_FP32_MIXED, 1e-5), (SMALL2D, srdr.SRDR_FP32_MIXED, 1e-5),
+    (WIDE3D, srdr.SRDR_FP64, 1e-12), (WIDE2D, srdr.SRDR_FP32_MIXED, 1e-5)])
 def test_stencil_matches_sliced_ell(spec, precision, tol):
     """The same body with the lattice stencil and with the sliced ELL over 40
     steps (damped and undamped): the stencil's pair gradients are evaluated
