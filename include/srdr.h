@@ -80,7 +80,7 @@ enum { SRDR_SWEEP_LAYOUT_3D = 0, SRDR_SWEEP_LAYOUT_2D = 1 };
  *   Explicit bodies step alone (batches refuse them).
  * precision: SRDR_FP64 computes everything in FP64; SRDR_FP32_MIXED runs the
  *   neighbour sums, stress and damping in FP32 and keeps the displacement as
- *   an FP32 hi plus a 10-bit lo per component (about 35 significant bits) and the kinetic-energy
+ *   an FP32 hi plus an FP32 lo per component (about 48 significant bits) and the kinetic-energy
  *   reduction in FP64.
  * dt: > 0 fixes the time step; 0 uses Eq. time-step-criterion with
  *   |v|max = 0 and |a|max = the largest body force, min'd with the implicit

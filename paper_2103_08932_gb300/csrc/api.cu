@@ -339,17 +339,19 @@ __global__ void k_read_uv(const int* __restrict__ perm, int n, const double* __r
                           const float* __restrict__ uhi, const float* __restrict__ ulo,
                           const T* __restrict__ v, double half_dt, int what, double* __restrict__ out)
 {
-    (void)ulo;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int i = perm ? perm[s] : s;  // null: arrays in original order
     float hf[3] = {0, 0, 0}, lf[3] = {0, 0, 0};
     if (!u) {
         const float4 r = reinterpret_cast<const float4*>(uhi)[s];
+        const float2 q = reinterpret_cast<const float2*>(ulo)[s];
         hf[0] = r.x;
         hf[1] = r.y;
         hf[2] = r.z;
-        lo_decode(hf, r.w, lf);
+        lf[0] = r.w;
+        lf[1] = q.x;
+        lf[2] = q.y;
     }
     for (int a = 0; a < 3; ++a) {
         double vv = (double)v[(size_t)s * 4 + a];
@@ -369,7 +371,6 @@ __global__ void k_write_uv(const int* __restrict__ perm, int n, const double* __
                            const double* __restrict__ vin, double half_dt, double* __restrict__ u,
                            float* __restrict__ uhi, float* __restrict__ ulo, T* __restrict__ v)
 {
-    (void)ulo;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int i = perm ? perm[s] : s;  // null: arrays in original order
@@ -387,7 +388,10 @@ __global__ void k_write_uv(const int* __restrict__ perm, int n, const double* __
             }
         }
     }
-    if (uin && !u) reinterpret_cast<float4*>(uhi)[s] = make_float4(h[0], h[1], h[2], lo_encode(h, l));
+    if (uin && !u) {
+        reinterpret_cast<float4*>(uhi)[s] = make_float4(h[0], h[1], h[2], l[0]);
+        reinterpret_cast<float2*>(ulo)[s] = make_float2(l[1], l[2]);
+    }
 }
 
 template <typename T>

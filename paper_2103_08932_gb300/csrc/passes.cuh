@@ -29,8 +29,8 @@ __device__ inline uint16_t ld_stream(const uint16_t* p)
 }
 
 // ------------------------------------------------------------------ layouts
-// u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 records [n][4]
-// (hi x, y, z and the packed lo of lo_encode; u = hi + lo).
+// u at the half step: FP64 [n][4] (x, y, z, 0), or FP32 (hi x, y, z, lo x)
+// [n][4] and (lo y, lo z) [n][2], u = hi + lo.
 // PB (P B0): the D x D entries of a particle, row-major, in pb_full whole
 // 16-byte chunks and pb_tail leftover entries; chunk c of all particles forms
 // one dense array (chunk c of particle j at 16-byte index c n + j), each
@@ -112,13 +112,14 @@ struct UAcc<double> {
 };
 template <>
 struct UAcc<float> {
-    // FP32 mixed: one record (hi x, y, z, packed lo), u = hi + lo
-    __device__ static void load(const double*, const float* hi, const float*, int j, float (&h)[3],
+    // FP32 mixed: (hi x, y, z, lo x) and (lo y, lo z), u = hi + lo
+    __device__ static void load(const double*, const float* hi, const float* lo, int j, float (&h)[3],
                                 float (&l)[3])
     {
         const float4 a = __ldg(reinterpret_cast<const float4*>(hi) + j);
+        const float2 b = __ldg(reinterpret_cast<const float2*>(lo) + j);
         h[0] = a.x; h[1] = a.y; h[2] = a.z;
-        lo_decode(h, a.w, l);
+        l[0] = a.w; l[1] = b.x; l[2] = b.y;
     }
     // (hi_i - hi_j) + (lo_i - lo_j): the hi difference is exact when the two
     // displacements are within a factor of two (Sterbenz), which is exactly
@@ -403,19 +404,50 @@ __global__ void __launch_bounds__(kThreads) k_pass_a(StepArgs<T> a)
 // a fixed offset (the same for the whole warp), leaving the L1 path to the
 // neighbour gathers.  Same table values in the same order as the global
 // table above, so the same bits.
-template <typename T, int D, int K>
+// CHECK: test each offset against the box; a warp whose lattice points all
+// lie at least the table's reach inside the box skips the test (every
+// neighbour exists).
+template <typename T, int D, int K, bool CHECK>
 __device__ inline void stencil_slots_tab(const StencilTab<T, K>& tb, const StepArgs<T>& a, int i, int x, int y,
                                          int z, int k0, int (&jj)[kUnroll], T (&gg)[kUnroll][D])
 {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
         const int k = k0 + u;
-        const bool in = (unsigned)(x + tb.dx[k]) < (unsigned)a.lx && (unsigned)(y + tb.dy[k]) < (unsigned)a.ly &&
-                        (unsigned)(z + tb.dz[k]) < (unsigned)a.lz;
-        jj[u] = in ? i + tb.delta[k] : i;
+        if constexpr (CHECK) {
+            const bool in = (unsigned)(x + tb.dx[k]) < (unsigned)a.lx &&
+                            (unsigned)(y + tb.dy[k]) < (unsigned)a.ly && (unsigned)(z + tb.dz[k]) < (unsigned)a.lz;
+            jj[u] = in ? i + tb.delta[k] : i;
+        } else {
+            jj[u] = i + tb.delta[k];
+        }
         gg[u][0] = tb.g[k][0];
         gg[u][1] = tb.g[k][1];
         if constexpr (D == 3) gg[u][2] = tb.g[k][2];
+    }
+}
+
+// lattice point (x, y, z) lies at least r points inside the box
+template <int D>
+__device__ inline bool lattice_inner(int x, int y, int z, int lx, int ly, int lz, int r)
+{
+    return x >= r && x < lx - r && y >= r && y < ly - r && (D == 2 || (z >= r && z < lz - r));
+}
+
+template <typename T, int D, int K, bool CHECK>
+__device__ inline void pass_a_sum_tab(const StencilTab<T, K>& tb, const StepArgs<T>& a, int i, int x, int y, int z,
+                                      const T (&xi)[3], const T (&li)[3], T (&G)[D][D])
+{
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
+        stencil_slots_tab<T, D, K, CHECK>(tb, a, i, x, y, z, k0, jj, gg);
+        T xj[kUnroll][3], lj[kUnroll][3];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) UAcc<T>::load(a.u, a.uhi, a.ulo, jj[u], xj[u], lj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) acc_grad<T, D>(G, xi, li, xj[u], lj[u], gg[u]);
     }
 }
 
@@ -425,9 +457,11 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_tab(StepArgs<T> a, const __
     static_assert(K % kUnroll == 0, "stencil tables are padded to the passes' batch");
     if (a.sc->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
     int x, y, z;
     lattice_xyz(i, a.lx, a.ly, x, y, z);
+    // one choice per warp (every lane votes before any leaves)
+    const bool inner = __all_sync(0xffffffffu, i < a.n && lattice_inner<D>(x, y, z, a.lx, a.ly, a.lz, tb.reach));
+    if (i >= a.n) return;
     T xi[3], li[3];
     UAcc<T>::load(a.u, a.uhi, a.ulo, i, xi, li);
     T G[D][D];
@@ -435,17 +469,10 @@ __global__ void __launch_bounds__(kThreads) k_pass_a_tab(StepArgs<T> a, const __
     for (int p = 0; p < D; ++p)
 #pragma unroll
         for (int q = 0; q < D; ++q) G[p][q] = 0;
-#pragma unroll
-    for (int k0 = 0; k0 < K; k0 += kUnroll) {
-        int jj[kUnroll];
-        T gg[kUnroll][D];
-        stencil_slots_tab<T, D, K>(tb, a, i, x, y, z, k0, jj, gg);
-        T xj[kUnroll][3], lj[kUnroll][3];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) UAcc<T>::load(a.u, a.uhi, a.ulo, jj[u], xj[u], lj[u]);
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) acc_grad<T, D>(G, xi, li, xj[u], lj[u], gg[u]);
-    }
+    if (inner)
+        pass_a_sum_tab<T, D, K, false>(tb, a, i, x, y, z, xi, li, G);
+    else
+        pass_a_sum_tab<T, D, K, true>(tb, a, i, x, y, z, xi, li, G);
     pass_a_epilogue<T, D, MAT>(a, i, G);
 }
 
@@ -583,8 +610,8 @@ __device__ inline void ke_last_block(const StepArgs<T>& a, double ke, int damped
     if (threadIdx.x == 0) a.sc->ke_ticket = 0;
 }
 
-// u <- u + d, FP64, or FP32 hi + packed lo (two-sum with renormalisation,
-// then lo re-encoded)
+// u <- u + d, FP64, or FP32 hi + lo (two-sum with renormalisation,
+// both parts stored as floats)
 template <typename T>
 __device__ inline void u_add(const StepArgs<T>& a, int i, const T (&d)[3]);
 template <>
@@ -612,12 +639,14 @@ template <>
 __device__ inline void u_add<float>(const StepArgs<float>& a, int i, const float (&d)[3])
 {
     float4* ph = reinterpret_cast<float4*>(a.uhi) + i;
-    float4 r = *ph;
-    float h[3] = {r.x, r.y, r.z}, l[3];
-    lo_decode(h, r.w, l);
+    float2* pl = reinterpret_cast<float2*>(a.ulo) + i;
+    const float4 r = *ph;
+    const float2 q = *pl;
+    float h[3] = {r.x, r.y, r.z}, l[3] = {r.w, q.x, q.y};
 #pragma unroll
     for (int c = 0; c < 3; ++c) two_sum_add(h[c], l[c], d[c]);
-    *ph = make_float4(h[0], h[1], h[2], lo_encode(h, l));
+    *ph = make_float4(h[0], h[1], h[2], l[0]);
+    *pl = make_float2(l[1], l[2]);
 }
 
 // ------------------------------------------------------------------ pass B
@@ -739,6 +768,23 @@ __device__ inline double pass_b_particle_st(const StepArgs<T>& a, int i, int fin
     return pass_b_epilogue<T, D>(a, i, acc, Pi, final_step);
 }
 
+template <typename T, int D, int K, bool CHECK>
+__device__ inline void pass_b_sum_tab(const StencilTab<T, K>& tb, const StepArgs<T>& a, int i, int x, int y, int z,
+                                      const T (&Pi)[D][D], T (&acc)[D])
+{
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += kUnroll) {
+        int jj[kUnroll];
+        T gg[kUnroll][D];
+        stencil_slots_tab<T, D, K, CHECK>(tb, a, i, x, y, z, k0, jj, gg);
+        T Pj[kUnroll][D][D];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, a.n, jj[u], Pj[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) acc_force<T, D>(acc, Pi, Pj[u], gg[u]);
+    }
+}
+
 // the force pass with the stencil table as a kernel parameter (see
 // k_pass_a_tab)
 template <typename T, int D, int K>
@@ -751,6 +797,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass_b_tab(StepArgs<T> a, const
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double ke = 0.0;
     if (i < a.n) {
+        // every offset tested against the box: a second, untested copy of
+        // the loop (as in the stress pass) spills at this kernel's 80
+        // registers and measured slower
         int x, y, z;
         lattice_xyz(i, a.lx, a.ly, x, y, z);
         T Pi[D][D];
@@ -758,17 +807,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass_b_tab(StepArgs<T> a, const
         T acc[D];
 #pragma unroll
         for (int p = 0; p < D; ++p) acc[p] = 0;
-#pragma unroll
-        for (int k0 = 0; k0 < K; k0 += kUnroll) {
-            int jj[kUnroll];
-            T gg[kUnroll][D];
-            stencil_slots_tab<T, D, K>(tb, a, i, x, y, z, k0, jj, gg);
-            T Pj[kUnroll][D][D];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) PBL<T, D>::load(a.PB, a.n, jj[u], Pj[u]);
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) acc_force<T, D>(acc, Pi, Pj[u], gg[u]);
-        }
+        pass_b_sum_tab<T, D, K, true>(tb, a, i, x, y, z, Pi, acc);
         ke = pass_b_epilogue<T, D>(a, i, acc, Pi, final_step);
     }
     if (final_step) ke_last_block(a, ke, 0);
@@ -897,7 +936,7 @@ StepArgs<T> make_step_args(srdr_body* b)
     a.v = static_cast<T*>(b->v);
     a.u = b->u;
     a.uhi = b->uhi;
-    a.ulo = nullptr;
+    a.ulo = b->ulo;
     a.flags = b->flags;
     a.mass = static_cast<const T*>(b->mass);
     a.ke_part = b->ke_part;
@@ -934,6 +973,7 @@ StencilTab<T, K> make_stencil_tab(const srdr_body* b)
     StencilTab<T, K> t{};
     for (int k = 0; k < K && k < (int)b->st_off_h.size(); ++k) {
         const int4 o = b->st_off_h[k];
+        t.reach = std::max(t.reach, std::max(std::abs(o.x), std::max(std::abs(o.y), std::abs(o.z))));
         t.delta[k] = o.w;
         t.dx[k] = o.x;
         t.dy[k] = o.y;

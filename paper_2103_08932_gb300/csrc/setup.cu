@@ -268,8 +268,8 @@ __global__ void k_gather(const int* __restrict__ perm, int n, const double* __re
     const double m = rho0 * (vol ? vol[i] : vol0);
     mass[s] = (T)m;
     minv[s] = (T)(1.0 / m);
-    // u at the half step, AoS padded to 4: FP64 [n][4] or FP32 records
-    // (hi x, y, z, packed lo)
+    // u at the half step, AoS padded to 4: FP64 [n][4], or FP32 hi and lo
+    // ((hi x, y, z, lo x) [n][4] and (lo y, lo z) [n][2])
     float h[3], l[3];
     for (int a = 0; a < 4; ++a) {
         double x = (u0 && a < 3) ? u0[(size_t)i * 3 + a] : 0.0;
@@ -280,8 +280,8 @@ __global__ void k_gather(const int* __restrict__ perm, int n, const double* __re
         }
     }
     if (uhi) {
-        (void)ulo;
-        reinterpret_cast<float4*>(uhi)[s] = make_float4(h[0], h[1], h[2], lo_encode(h, l));
+        reinterpret_cast<float4*>(uhi)[s] = make_float4(h[0], h[1], h[2], l[0]);
+        reinterpret_cast<float2*>(ulo)[s] = make_float2(l[1], l[2]);
     }
 }
 
@@ -896,13 +896,15 @@ srdr_status relayout_stencil(srdr_body* b)
     k_perm_rows<T><<<nb, kThreads, 0, st>>>(perm, n, 4, static_cast<const T*>(b->v), v);
     k_perm_cols<T><<<nb, kThreads, 0, st>>>(perm, n, dim * dim, static_cast<const T*>(b->B0), B0);
     double* u = nullptr;
-    float* uhi = nullptr;
+    float *uhi = nullptr, *ulo = nullptr;
     if (b->u) {
         SRDR_TRY(dalloc(b, &u, (size_t)n * 4));
         k_perm_rows<double><<<nb, kThreads, 0, st>>>(perm, n, 4, b->u, u);
     } else {
         SRDR_TRY(dalloc(b, &uhi, (size_t)n * 4));
+        SRDR_TRY(dalloc(b, &ulo, (size_t)n * 2));
         k_perm_rows<float><<<nb, kThreads, 0, st>>>(perm, n, 4, b->uhi, uhi);
+        k_perm_rows<float><<<nb, kThreads, 0, st>>>(perm, n, 2, b->ulo, ulo);
     }
     T* bf = nullptr;
     if (b->bf) {
@@ -922,6 +924,7 @@ srdr_status relayout_stencil(srdr_body* b)
     SRDR_TRY(dev_free(b, b->B0));
     SRDR_TRY(dev_free(b, b->u));
     SRDR_TRY(dev_free(b, b->uhi));
+    SRDR_TRY(dev_free(b, b->ulo));
     SRDR_TRY(dev_free(b, b->bf));
     b->mass_sw = b->mass;
     b->vs = b->v;  // the sorted records become the sweep's copy
@@ -932,6 +935,7 @@ srdr_status relayout_stencil(srdr_body* b)
     b->B0 = B0;
     b->u = u;
     b->uhi = uhi;
+    b->ulo = ulo;
     b->bf = bf;
     b->pidx = b->perm;
     b->stencil = 1;
@@ -1033,6 +1037,7 @@ srdr_status build_typed(srdr_body* b, int64_t n64, const double* r0_host, const 
         SRDR_TRY(dalloc(b, &b->u, (size_t)n * 4));
     } else {
         SRDR_TRY(dalloc(b, &b->uhi, (size_t)n * 4));
+        SRDR_TRY(dalloc(b, &b->ulo, (size_t)n * 2));
     }
     k_gather<T><<<nblocks(n), kThreads, 0, st>>>(b->perm, n, r0aos, vol, b->vol0, fl, u0, cell_orig,
                                                  b->desc.rho0, b->inv, b->cell_of, b->r0, b->flags,

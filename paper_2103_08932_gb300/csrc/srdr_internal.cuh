@@ -5,10 +5,10 @@
 // sorted by (cell id, original id), the canonical order of the splitting
 // cell-linked list):
 //   r0    FP64 [3][n] SoA reference positions
-//   u     FP64 [n][4] (FP64 mode) or FP32 records [n][4] (FP32 mode: hi and
-//         a packed 10-bit lo, u = hi + lo), held at the half step
-//         u^{n+1/2}; AoS so that one neighbour gather is one (FP32) or two
-//         (FP64) 16-byte loads
+//   u     FP64 [n][4] (FP64 mode) or FP32 hi and lo (FP32 mode: (hi x, y,
+//         z, lo x) [n][4] and (lo y, lo z) [n][2], u = hi + lo), held at
+//         the half step u^{n+1/2}; AoS so that one neighbour gather is a
+//         16-byte and an 8-byte load (FP32) or two 16-byte loads (FP64)
 //   v     T [n][4] velocity records (vx, vy, vz, 1/m): one 16-byte (FP32) or
 //         two 16-byte (FP64) accesses per particle
 //   B0    T [D*D][n] row-major tensor components, SoA (read by the owner only)
@@ -67,42 +67,10 @@ struct DevScalars {
     int pad_;
 };
 
-// FP32-mixed displacement record (float4): x, y, z hold hi = fl(u); w holds
-// lo = u - hi of each component as a signed 10-bit multiple of ulp(hi)/1024
-// (|lo| <= ulp(hi)/2 after renormalisation).  u = hi + lo then carries about
-// 35 significant bits, and a neighbour gather is one 16-byte load.  ulp/1024
-// and its inverse are powers of two, so scaling is exact; |hi| < 2^-93
-// keeps lo = 0.
-__device__ inline float lo_unit(float h)
-{
-    const unsigned e = (__float_as_uint(h) >> 23) & 0xffu;
-    return e > 33u ? __uint_as_float((e - 33u) << 23) : 0.0f;
-}
-__device__ inline float lo_inv_unit(float h)
-{
-    const unsigned e = (__float_as_uint(h) >> 23) & 0xffu;
-    return (e > 33u && e < 255u) ? __uint_as_float((287u - e) << 23) : 0.0f;
-}
-__device__ inline float lo_encode(const float (&h)[3], const float (&l)[3])
-{
-    unsigned w = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        int q = __float2int_rn(l[c] * lo_inv_unit(h[c]));
-        q = q < -511 ? -511 : (q > 511 ? 511 : q);
-        w |= ((unsigned)q & 1023u) << (10 * c);
-    }
-    return __uint_as_float(w);
-}
-__device__ inline void lo_decode(const float (&h)[3], float packed, float (&l)[3])
-{
-    const unsigned w = __float_as_uint(packed);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int q = (int)(w << (22 - 10 * c)) >> 22;  // sign-extended 10-bit field
-        l[c] = (float)q * lo_unit(h[c]);
-    }
-}
+// FP32-mixed displacement: u = hi + lo per component, hi = fl(u) and
+// lo = fl(u - hi), stored as uhi [n][4] = (hi x, hi y, hi z, lo x) and
+// ulo [n][2] = (lo y, lo z).  u then carries about 48 significant bits; a
+// neighbour gather is one 16-byte and one 8-byte load with nothing to decode.
 
 // 1/2 m |v|^2 of one particle with explicit roundings: the same bits in
 // every kernel that evaluates it (no contraction choice left to the
@@ -146,6 +114,7 @@ struct StencilTab {
     int delta[K];
     int dx[K], dy[K], dz[K];
     T g[K][3];
+    int reach;  // the largest |component| of an offset
 };
 constexpr int kStencilK3 = 80;
 constexpr int kStencilK2 = 24;
@@ -168,8 +137,8 @@ struct StepArgs {
     const int* dflag;            // device-decided damping of this step (graph replay), else null
     T* __restrict__ v;          // [n][4] (vx, vy, vz, 1/m)
     double* __restrict__ u;     // [3][n] FP64 mode
-    float* __restrict__ uhi;    // [n][4] FP32 mode: (hi x, y, z, packed lo), u = hi + lo
-    float* __restrict__ ulo;    // unused (null)
+    float* __restrict__ uhi;    // [n][4] FP32 mode: (hi x, y, z, lo x), u = hi + lo
+    float* __restrict__ ulo;    // [n][2] FP32 mode: (lo y, lo z)
     const uint8_t* __restrict__ flags;
     const T* __restrict__ mass;
     double* __restrict__ ke_part;
@@ -316,8 +285,8 @@ struct srdr_body {
     void* srd = nullptr;         //   (prepare_sweep; B_j = c w_ij with the body's c)
     void* v = nullptr;          // T [n][4] (vx, vy, vz, 1/m)
     double* u = nullptr;        // FP64 [3][n]
-    float* uhi = nullptr;       // [n][4] FP32 mode: (hi x, y, z, packed lo)
-    float* ulo = nullptr;       // unused (null)
+    float* uhi = nullptr;       // [n][4] FP32 mode: (hi x, y, z, lo x)
+    float* ulo = nullptr;       // [n][2] FP32 mode: (lo y, lo z)
     double* ke_part = nullptr;
     int ke_blocks = 0;
     srdr::DevScalars* sc = nullptr;
@@ -435,7 +404,7 @@ srdr_status prepare_sweep(srdr_body* b);
 // brick size; b->bricks_built = 1 when built, -1 when a halo does not fit
 srdr_status build_bricks(srdr_body* b);
 // shared memory of the tiled passes per block for a halo of h particles
-inline size_t tile_smem_a(size_t tsize, int h) { return (tsize == 4 ? (size_t)16 : (size_t)32) * h; }
+inline size_t tile_smem_a(size_t tsize, int h) { return (tsize == 4 ? (size_t)24 : (size_t)32) * h; }
 inline size_t tile_smem_b(size_t tsize, int dim, int h) { return 16 * (size_t)pb_chunks(tsize, dim) * h; }
 constexpr size_t kTileSmemMax = 200 * 1024;
 // kernel-class timing (api.cu): begin/end an interval of class k

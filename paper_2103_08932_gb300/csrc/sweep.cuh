@@ -494,14 +494,18 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
                         // half the step: (c/2) w = B/2 exactly (a power-of-two scaling)
                         const T B = T(0.5) * r.B;
                         V4 xi = sv[li], xj = sv[j];
-                        const T mj = T(1) / xj.w;
-                        const T den = mi * mj - (mi + mj) * B;
+                        // m_j B / den and m_i B / den, den = m_i m_j - (m_i + m_j) B,
+                        // multiplied through by w_j = 1 / m_j (the record's fourth
+                        // entry): one division per pair
+                        const T wj = xj.w;
+                        const T q = B / (mi - (mi * wj + T(1)) * B);
+                        const T qj = mi * wj * q;
                         T pi_[3] = {xi.x, xi.y, xi.z}, pj_[3] = {xj.x, xj.y, xj.z};
 #pragma unroll
                         for (int d = 0; d < D; ++d) {
                             const T vij = pi_[d] - pj_[d];
-                            pi_[d] += mj * B * vij / den;
-                            pj_[d] += -mi * B * vij / den;
+                            pi_[d] += q * vij;
+                            pj_[d] -= qj * vij;
                         }
                         sv[li] = V4{pi_[0], pi_[1], pi_[2], xi.w};
                         sv[j] = V4{pj_[0], pj_[1], pj_[2], xj.w};

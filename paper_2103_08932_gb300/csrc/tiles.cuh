@@ -73,15 +73,16 @@ __device__ inline void stage_halo_u64(unsigned char* dst, const unsigned char* s
     __syncthreads();
 }
 
-// u of halo record l from shared memory (FP32: hi and packed lo)
+// u of halo record l from shared memory (FP32: (hi, lo x) records, then the
+// (lo y, lo z) pairs after all nh of them)
 template <typename T>
 __device__ inline void u_smem(const unsigned char* s, int nh, int l, T (&x)[3], T (&lo)[3])
 {
-    (void)nh;
     if constexpr (sizeof(T) == 4) {
         const float4 a = reinterpret_cast<const float4*>(s)[l];
+        const float2 b = reinterpret_cast<const float2*>(s + (size_t)nh * 16)[l];
         x[0] = a.x; x[1] = a.y; x[2] = a.z;
-        lo_decode(x, a.w, lo);
+        lo[0] = a.w; lo[1] = b.x; lo[2] = b.y;
     } else {
         const double2* q = reinterpret_cast<const double2*>(s) + (size_t)l * 2;
         const double2 a = q[0], b = q[1];
@@ -131,10 +132,14 @@ __global__ void __launch_bounds__(kTileThreads) k_pass_a_tiled(StepArgs<T> a, Ti
     const BrickInfo bi = tl.info[blockIdx.x];
     const int nh = bi.nhalo;
     if constexpr (sizeof(T) == 4) {
-        // one 16-byte record (hi, packed lo) per halo particle
+        // a 16-byte (hi, lo x) record and an 8-byte (lo y, lo z) pair per
+        // halo particle
         const int* hl = tl.halo + bi.halo_base;
-        for (int h = threadIdx.x; h < nh; h += blockDim.x)
-            cp_async16(tsm + (size_t)h * 16, a.uhi + (size_t)__ldg(hl + h) * 4);
+        for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+            const size_t j = (size_t)__ldg(hl + h);
+            cp_async16(tsm + (size_t)h * 16, a.uhi + j * 4);
+            cp_async8(tsm + (size_t)nh * 16 + (size_t)h * 8, a.ulo + j * 2);
+        }
         cp_async_wait_all_t();
         __syncthreads();
     } else {
