@@ -788,7 +788,7 @@ __device__ inline void pass_b_sum_tab(const StencilTab<T, K>& tb, const StepArgs
 // the force pass with the stencil table as a kernel parameter (see
 // k_pass_a_tab)
 template <typename T, int D, int K>
-__global__ void __launch_bounds__(kThreads, 3) k_pass_b_tab(StepArgs<T> a, const __grid_constant__ StencilTab<T, K> tb,
+__global__ void __launch_bounds__(kThreads, 4) k_pass_b_tab(StepArgs<T> a, const __grid_constant__ StencilTab<T, K> tb,
                                                            int final_step)
 {
     static_assert(K % kUnroll == 0, "stencil tables are padded to the passes' batch");
