@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-l2-flush", action="store_true",
+                    help="skip the l2_flushed record (steps timed one at a time after a 256 MB write)")
     ap.add_argument("--sweep-sync", choices=["auto", "barrier", "cells"], default="auto",
                     help="synchronisation of the damping sweep's colour phases (default: autotuned)")
     ap.add_argument("--workload", choices=["plate", "batched", "served", "block", "compare", "strength",
@@ -339,6 +341,30 @@ def run_gpu(args):
         except (OSError, ValueError):
             traffic = None
 
+    # the same steps with L2 flushed before each one: 256 MB written on the
+    # body's stream, then the step timed alone.  The passes' per-particle
+    # arrays (about 150 B per particle) fit in L2 and may stay there between
+    # undamped steps of the continuous run above; the sweep's slot records
+    # (8 B per pair) pass through L2 on every damped step.  A step timed
+    # alone also waits for its own launches, so this rate is a lower bound.
+    l2f = None
+    if not args.no_l2_flush:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        nfl = min(args.steps, 400)
+        d0 = body.stats()["damped_steps"]
+        tot = 0.0
+        for s in range(nfl):
+            flush.fill_(s & 0xFF)
+            e0.record(stream)
+            body.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        l2f = {"steps": nfl, "damped_steps": int(body.stats()["damped_steps"] - d0),
+               "ms_per_step": tot / nfl, "value": world * n / (tot / nfl / 1e3),
+               "flush": "256 MB written before each step; each step timed alone on the body's stream"}
+        del flush
+
     # end to end through the C ABI with host buffers: create the body from
     # host particle arrays (H2D), run the steps, read the displacement (D2H)
     e2e = None
@@ -398,7 +424,11 @@ def run_gpu(args):
                        "sweep_cells_per_warp": st1.get("sweep_cells_per_warp"),
                        "sweep_sync": {srdr.SRDR_SWEEP_CELLS: "cell-wise waits",
                                       srdr.SRDR_SWEEP_BARRIER: "grid barriers"}.get(st1.get("sweep_sync")),
-                       "l2": "working set ~0.9 GB > 129 MB L2 (no flush)"},
+                       "l2": (f"no flush in the timed region: body data {(150 * n + 8 * body.nnz) / 1e6:.0f} MB "
+                              f"> 129 MB L2, of which the sweep's slot records ({8 * body.nnz / 1e6:.0f} MB) "
+                              f"stream through L2 on every damped step while the passes' per-particle arrays "
+                              f"({150 * n / 1e6:.0f} MB) may stay in L2 between undamped steps; `l2_flushed` "
+                              f"times steps after a 256 MB write")},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "algorithmic_bytes": ab[dom]},
@@ -409,6 +439,7 @@ def run_gpu(args):
             "served": served,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "l2_flushed": l2f,
             "gpu_launches": launches,
             "clocks": clocks,
         }
