@@ -268,6 +268,18 @@ srdr_status srdr_body_tune(srdr_body* body, int sweep_cells_per_warp, int sweep_
 enum { SRDR_SWEEP_AUTO = 0, SRDR_SWEEP_BARRIER = 1, SRDR_SWEEP_CELLS = 2 };
 srdr_status srdr_body_sweep_sync(srdr_body* body, int mode);
 
+/* Width of the damping sweep's serial chain (Sec. 3.1's local update of one
+ * particle after another, Sec. 3.4's colour sweep): the cell-wise sweep runs
+ * one cell per warp, and the chain of a cell's particle updates uses 32 lanes
+ * (each row's neighbours spread over 32 lanes, a 5-level reduction per
+ * update) or 16 (one reduction level fewer, the whole warp still waiting,
+ * copying and writing back).  The sums follow the same 32-lane order either
+ * way, so results are bitwise the same.  lanes = 0 (the default) lets the
+ * autotuner choose; 16 or 32 fixes it (with cell-wise waits, one cell per
+ * warp, the warps per block of srdr_body_tune).  SRDR_ERR_INVALID for another
+ * value or when the body asks for grid barriers (srdr_body_sweep_sync). */
+srdr_status srdr_body_sweep_lanes(srdr_body* body, int lanes);
+
 /* Test hook of the failure path above: makes every wait of the body's next
  * damping sweep run out (it sets the synchronisation words to counts that no
  * cell reaches), so that the sweep ends with the body's status set after

@@ -665,6 +665,7 @@ srdr_status srdr_body_tune(srdr_body* b, int cells_per_warp, int warps_per_block
         b->sweep_tuned = 1;
         b->sweep_cells_per_warp = cells_per_warp;
         b->sweep_warps_per_block = warps_per_block;
+        b->sweep_chain16 = 0;
         // cell-wise waits pair with one cell per warp unless asked for
         b->sweep_cellwise = b->sweep_sync == SRDR_SWEEP_CELLS ||
                             (b->sweep_sync == SRDR_SWEEP_AUTO && cells_per_warp == 1);
@@ -687,6 +688,31 @@ srdr_status srdr_body_sweep_sync(srdr_body* b, int mode)
         b->sweep_tuned = 0;
     else
         b->sweep_cellwise = mode == SRDR_SWEEP_CELLS;
+    return SRDR_OK;
+}
+
+srdr_status srdr_body_sweep_lanes(srdr_body* b, int lanes)
+{
+    if (!b || (lanes != 0 && lanes != 16 && lanes != 32)) {
+        set_error("sweep chain lanes must be 0 (autotuned), 16 or 32");
+        return SRDR_ERR_INVALID;
+    }
+    if (lanes != 0 && b->sweep_sync == SRDR_SWEEP_BARRIER) {
+        set_error("the chain width is a choice of the cell-wise sweep (the body asks for grid barriers)");
+        return SRDR_ERR_INVALID;
+    }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);  // captured with the old kernel
+        b->graph = nullptr;
+    }
+    if (lanes == 0) {
+        b->sweep_tuned = 0;
+        return SRDR_OK;
+    }
+    b->sweep_tuned = 1;
+    b->sweep_cells_per_warp = 1;
+    b->sweep_cellwise = 1;
+    b->sweep_chain16 = lanes == 16;
     return SRDR_OK;
 }
 

@@ -315,6 +315,7 @@ struct srdr_body {
     void* bf = nullptr;              // T [n][4] rotational body force per particle (twist)
     int sweep_cells_per_warp = 2;    // cells per warp of the sweep kernel (1, 2, 4)
     int sweep_warps_per_block = 1;   // warps per block of the sweep kernel (1, 4)
+    int sweep_chain16 = 0;           // cell-wise sweep with the chain on 16 lanes of each warp
     int sweep_tuned = 0;
     int sweep_smem = 0;
     int sweep_rows_global = 0;       // slot records read from global memory (staging does not fit)

@@ -105,7 +105,7 @@ struct SweepLaunch {
     unsigned* sync = nullptr;
 };
 
-template <typename T, int D, int G, int W>
+template <typename T, int D, int G, int W, int H = 0>
 srdr_status sweep_launch_gw(srdr_body* b, SweepLaunch<T, D>* out)
 {
     // the rows are staged in shared memory when a cell's fit, else read
@@ -120,7 +120,7 @@ srdr_status sweep_launch_gw(srdr_body* b, SweepLaunch<T, D>* out)
         set_error("damping sweep needs %zu bytes of shared memory per block (limit 227 KB)", smem);
         return SRDR_ERR_INVALID;
     }
-    const void* fn = b->sweep_cellwise ? (const void*)k_sweep_flow<T, D, G, W>
+    const void* fn = b->sweep_cellwise ? (const void*)k_sweep_flow<T, D, G, W, H>
                                        : (const void*)k_sweep_all<T, D, G, W>;
     if (smem > 48 * 1024)
         SRDR_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -146,6 +146,9 @@ srdr_status sweep_launch_gw(srdr_body* b, SweepLaunch<T, D>* out)
 template <typename T, int D>
 srdr_status sweep_launch(srdr_body* b, SweepLaunch<T, D>* out)
 {
+    if (b->sweep_chain16 && b->sweep_cellwise && b->sweep_cells_per_warp == 1)
+        return b->sweep_warps_per_block == 4 ? sweep_launch_gw<T, D, 1, 4, 1>(b, out)
+                                             : sweep_launch_gw<T, D, 1, 1, 1>(b, out);
     const int key = b->sweep_cells_per_warp * 10 + b->sweep_warps_per_block;
     switch (key) {
     case 11: return sweep_launch_gw<T, D, 1, 1>(b, out);
@@ -159,7 +162,8 @@ srdr_status sweep_launch(srdr_body* b, SweepLaunch<T, D>* out)
 
 // Autotuner of the sweep's mapping: time G = 1 or 2 cells per warp with
 // W = 1 or 4 warps per block, with cell-wise waits and with grid barriers
-// (unless one of them is asked for), one warm-up and one timed launch each,
+// (unless one of them is asked for), and the cell-wise sweep with its chain
+// on 16 lanes of each warp, one warm-up and one timed launch each,
 // on a scratch copy of v (the sweep writes v, the body's state must not
 // change) and keep the fastest.  G = 4 (measured slower on every body tried) stays
 // available through srdr_body_tune.  The sweep's
@@ -186,17 +190,22 @@ srdr_status autotune_sweep(srdr_body* b)
     SRDR_CK(cudaEventCreate(&e1));
     float best = 3.0e38f;
     int best_g = b->sweep_cells_per_warp, best_w = b->sweep_warps_per_block, best_c = b->sweep_cellwise;
+    int best_h = 0;
     for (int cw : {1, 0})
     for (int g : {1, 2})
+    for (int h : {0, 1})
         for (int w : {1, 4}) {
             if ((cw && b->sweep_sync == SRDR_SWEEP_BARRIER) || (!cw && b->sweep_sync == SRDR_SWEEP_CELLS))
                 continue;
             // cell-wise waits with one cell per warp only: two groups of a
             // warp would take turns, one polling while the other's chain waits
             if (cw && g > 1) continue;
+            // the 16-lane chain: cell-wise waits, one cell per warp
+            if (h && (!cw || g != 1)) continue;
             b->sweep_cellwise = cw;
             b->sweep_cells_per_warp = g;
             b->sweep_warps_per_block = w;
+            b->sweep_chain16 = h;
             SweepLaunch<T, D> sl;
             if (sweep_launch<T, D>(b, &sl) != SRDR_OK) continue;  // e.g. too much shared memory
             sw.rows_global = b->sweep_rows_global;  // the staging this mapping can afford
@@ -226,11 +235,13 @@ srdr_status autotune_sweep(srdr_body* b)
                 best_g = g;
                 best_w = w;
                 best_c = cw;
+                best_h = h;
             }
         }
     b->sweep_cells_per_warp = best_g;
     b->sweep_warps_per_block = best_w;
     b->sweep_cellwise = best_c;
+    b->sweep_chain16 = best_h;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     SRDR_TRY(dev_free(b, tflag));

@@ -301,42 +301,17 @@ __device__ inline CellStage stage_cell(const SweepArgs<T>& a, int c, const CellS
     return st;
 }
 
-// Sweep the staged cell: copy the footprint's velocity records from L2 into
-// shared memory, then apply the local operators of its particles in order
-// (mode 0), in reverse order (mode 1) or in order and then in reverse order
-// (mode 2: the last colour's forward and backward phases, fused since its
-// cells' footprints are disjoint), then write the footprint back through L2.
+// The serial chain of a staged cell (run_cell): the local operators of its
+// particles in order, in reverse order, or both (mode 0, 1, 2), on L lanes
+// (gmask) of the group.
 template <typename T, int D, int L>
-__device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int mode,
-                                const CellSmem<T, D>& s, int gl, unsigned gmask)
+__device__ inline void chain_cell(const SweepArgs<T>& a, const CellStage& st, int mode, const CellSmem<T, D>& s,
+                                  const SweepSlot<T>* __restrict__ rec, int gl, unsigned gmask)
 {
     using V4 = vec4_t<T>;
     const int np = st.np, p0 = st.p0, my_off = st.my_off;
-    const int Ftot = st.fr.total;
     V4* sv = s.sv;
-    // entry k of the cell's rows at rec[k - p0]: staged in shared memory, or
-    // (cells whose rows do not fit) read through the caches
-    const SweepSlot<T>* rec =
-        a.rows_global ? a.rec + p0 : s.srec + (p0 & (16 / (int)sizeof(SweepSlot<T>) - 1));
-    const int* sfoot = s.sfoot;
-    if (a.foot_tab) cp_async_wait_all();  // the touched list arrives by cp.async
-    __syncwarp(gmask);  // the footprint table written by other lanes of the group
-
-    // velocity records from L2 straight into shared memory
-    for (int q = gl; q < Ftot; q += L) {
-        const T* src = a.v + (size_t)sfoot[q] * 4;
-        if constexpr (sizeof(T) == 4) {
-            cp_async16s(sv + q, src);
-        } else {
-            cp_async16s(reinterpret_cast<double2*>(sv + q), src);
-            cp_async16s(reinterpret_cast<double2*>(sv + q) + 1, src + 2);
-        }
-    }
-    if (gl == 0) sv[a.max_foot] = V4{T(0), T(0), T(0), T(0)};
-    cp_async_wait_all();
-    __syncwarp(gmask);
     const int pad = a.max_foot;  // the zero record: padded slots read and write it with B = 0
-
     for (int dir = mode == 1 ? 1 : 0; dir <= (mode == 0 ? 0 : 1); ++dir) {
     const int backward = dir;
     if (!a.pairwise) {
@@ -516,6 +491,53 @@ __device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int 
         __syncwarp(gmask);
     }
     }  // dir
+}
+
+// Sweep the staged cell: copy the footprint's velocity records from L2 into
+// shared memory, then apply the local operators of its particles in order
+// (mode 0), in reverse order (mode 1) or in order and then in reverse order
+// (mode 2: the last colour's forward and backward phases, fused since its
+// cells' footprints are disjoint), then write the footprint back through L2.
+// The copies and the write-back use the group's L lanes, the chain CL of
+// them (CL < L only for a group that is a whole warp: lanes 0..CL-1).
+template <typename T, int D, int L, int CL = L>
+__device__ inline void run_cell(const SweepArgs<T>& a, const CellStage& st, int mode,
+                                const CellSmem<T, D>& s, int gl, unsigned gmask)
+{
+    static_assert(CL == L || L == 32, "a shorter chain needs a whole-warp group");
+    using V4 = vec4_t<T>;
+    const int p0 = st.p0;
+    const int Ftot = st.fr.total;
+    V4* sv = s.sv;
+    // entry k of the cell's rows at rec[k - p0]: staged in shared memory, or
+    // (cells whose rows do not fit) read through the caches
+    const SweepSlot<T>* rec =
+        a.rows_global ? a.rec + p0 : s.srec + (p0 & (16 / (int)sizeof(SweepSlot<T>) - 1));
+    const int* sfoot = s.sfoot;
+    if (a.foot_tab) cp_async_wait_all();  // the touched list arrives by cp.async
+    __syncwarp(gmask);  // the footprint table written by other lanes of the group
+
+    // velocity records from L2 straight into shared memory
+    for (int q = gl; q < Ftot; q += L) {
+        const T* src = a.v + (size_t)sfoot[q] * 4;
+        if constexpr (sizeof(T) == 4) {
+            cp_async16s(sv + q, src);
+        } else {
+            cp_async16s(reinterpret_cast<double2*>(sv + q), src);
+            cp_async16s(reinterpret_cast<double2*>(sv + q) + 1, src + 2);
+        }
+    }
+    if (gl == 0) sv[a.max_foot] = V4{T(0), T(0), T(0), T(0)};
+    cp_async_wait_all();
+    __syncwarp(gmask);
+    // the chain on CL lanes: all L lanes of the group (one shuffle level per
+    // halving of the lanes fewer with CL < L; the sums follow the same 32-lane
+    // order either way), the others wait for it before the write-back
+    if constexpr (CL == L)
+        chain_cell<T, D, L>(a, st, mode, s, rec, gl, gmask);
+    else if (gl < CL)
+        chain_cell<T, D, CL>(a, st, mode, s, rec, gl, (1u << CL) - 1u);
+    __syncwarp(gmask);
     // write the footprint back (through L2: other SMs read it after the barrier)
     for (int q = gl; q < Ftot; q += L) stcg_v4<T>(a.v, sfoot[q], sv[q]);
     __syncwarp(gmask);
@@ -698,11 +720,15 @@ __device__ inline bool flow_wait(const SweepArgs<T>& a, const unsigned* done, un
     return __all_sync(gmask, ok);
 }
 
-template <typename T, int D, int G, int W>
+// H: one cell per warp whose chain runs on 16 lanes (G = 1), the whole warp
+// waiting, copying and writing back
+template <typename T, int D, int G, int W, int H = 0>
 __global__ void __launch_bounds__(32 * W) k_sweep_flow(SweepArgs<T> a, const int* __restrict__ colour_ptr,
                                                        int ncolours, unsigned* flow)
 {
+    static_assert(H == 0 || G == 1, "the 16-lane chain takes one cell per warp");
     constexpr int L = 32 / G;
+    constexpr int CL = H ? 16 : L;
     if (*(volatile int*)&a.sc->done) return;
     if (a.dflag && *a.dflag == 0) return;
     if (*(volatile int*)&a.sc->status == DEV_TIMEOUT) return;  // counts left inconsistent: host resets them
@@ -735,7 +761,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_flow(SweepArgs<T> a, const int
                 ok = false;
                 break;
             }
-            run_cell<T, D, L>(a, st, mode, s, gl, gmask);
+            run_cell<T, D, L, CL>(a, st, mode, s, gl, gmask);
             if (gl == 0) {
                 __threadfence();  // the group's write-back (ordered by run_cell's __syncwarp) first
                 atomicAdd(done + cell, mode == 2 ? 2u : 1u);

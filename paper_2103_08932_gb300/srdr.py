@@ -52,7 +52,7 @@ EXPORTS = [
     "srdr_body_read_field", "srdr_body_destroy", "srdr_last_error", "srdr_philox4x64_10",
     "srdr_random_phi", "srdr_body_profile", "srdr_body_kernel_times",
     "srdr_kinetic_energy_noalloc", "srdr_body_tune", "srdr_desc_particle_count",
-    "srdr_body_pass_mapping", "srdr_body_sweep_sync", "srdr_body_debug_stall_sweep",
+    "srdr_body_pass_mapping", "srdr_body_sweep_sync", "srdr_body_sweep_lanes", "srdr_body_debug_stall_sweep",
     "srdr_batch_create", "srdr_batch_step", "srdr_batch_run", "srdr_batch_info", "srdr_batch_mode",
     "srdr_batch_destroy", "srdr_batch_relax", "srdr_server_create", "srdr_server_configure",
     "srdr_server_submit", "srdr_server_poll", "srdr_server_wait", "srdr_server_stats",
@@ -142,6 +142,7 @@ def lib():
         "srdr_body_kernel_times": (st, [p, C.POINTER(srdr_kernel_times)]),
         "srdr_body_tune": (st, [p, C.c_int, C.c_int]),
         "srdr_body_pass_mapping": (st, [p, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "srdr_body_sweep_lanes": (st, [p, C.c_int]),
         "srdr_body_sweep_sync": (st, [p, C.c_int]),
         "srdr_body_debug_stall_sweep": (st, [p]),
         "srdr_desc_particle_count": (st, [C.POINTER(srdr_body_desc), C.POINTER(i64)]),
@@ -292,6 +293,10 @@ class Body:
     def sweep_sync(self, mode=0):
         """SRDR_SWEEP_AUTO (0), SRDR_SWEEP_BARRIER (1) or SRDR_SWEEP_CELLS (2)."""
         _check(lib().srdr_body_sweep_sync(self.h, int(mode)))
+
+    def sweep_lanes(self, lanes=0):
+        """Width of the sweep's serial chain: 0 (autotuned), 16 or 32."""
+        _check(lib().srdr_body_sweep_lanes(self.h, int(lanes)))
 
     def debug_stall_sweep(self):
         """Make every wait of the next damping sweep run out (failure-path test hook)."""

@@ -62,6 +62,7 @@ def test_entry_points_reject_null_handles_without_gpu(L):
     their handles on the host before any device call."""
     calls = [
         lambda: L.srdr_body_sweep_sync(None, srdr.SRDR_SWEEP_CELLS),
+        lambda: L.srdr_body_sweep_lanes(None, 16),
         lambda: L.srdr_body_debug_stall_sweep(None),
         lambda: L.srdr_body_tune(None, 1, 1),
         lambda: L.srdr_body_pass_mapping(None, srdr.SRDR_PASS_SELL, 0, 0, 0),

@@ -531,6 +531,33 @@ def test_stencil_matches_sliced_ell(spec, precision, tol):
     assert np.array_equal(a.field(srdr.SRDR_FIELD_B0), b.field(srdr.SRDR_FIELD_B0))
 
 
+@pytest.mark.parametrize("spec,precision,damping", [
+    (SMALL3D, srdr.SRDR_FP32_MIXED, srdr.SRDR_DAMP_PARTICLE), (SMALL3D, srdr.SRDR_FP64, srdr.SRDR_DAMP_PARTICLE),
+    (SMALL2D, srdr.SRDR_FP32_MIXED, srdr.SRDR_DAMP_PARTICLE), (SMALL3D, srdr.SRDR_FP64, srdr.SRDR_DAMP_PAIRWISE)])
+def test_sweep_chain_widths_are_bitwise_equal(spec, precision, damping):
+    """The cell-wise sweep with each cell's chain on 32 lanes and on 16 lanes
+    (one reduction level fewer, the rest of the warp waiting, copying and
+    writing back) sums in the same 32-lane order: the states agree bit for
+    bit over 30 steps with damped steps among them."""
+    bodies = []
+    for lanes in (32, 16):
+        b = gpu_for(spec, precision=precision, damping=damping)
+        b.sweep_lanes(lanes)
+        b.step(30)
+        bodies.append(b)
+    a, b = bodies
+    assert 0 < a.stats()["damped_steps"] == b.stats()["damped_steps"]
+    assert np.array_equal(a.velocity(), b.velocity())
+    assert np.array_equal(a.displacement(), b.displacement())
+    assert a.stats()["ke"] == b.stats()["ke"]
+    with pytest.raises(srdr.SrdrError):
+        a.sweep_lanes(8)
+    barrier = gpu_for(spec, precision=precision, damping=damping)
+    barrier.sweep_sync(srdr.SRDR_SWEEP_BARRIER)
+    with pytest.raises(srdr.SrdrError):
+        barrier.sweep_lanes(16)
+
+
 # ------------------------------------------------------------------ explicit comparator
 @pytest.mark.parametrize("spec", [S.cantilever_2d(S.NEO_HOOKEAN), SMALL3D])
 def test_explicit_comparator_fp64_matches_oracle(spec):
